@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test checks the oracle against the mathematics or the paper:
+  * the plain Thomas solver against a dense LU solve;
+  * Kolmogorov's closed-form Gaussian solution of u_t + v u_x = u_vv (first order
+    under joint refinement of hx and dt: upwind transport + implicit Euler);
+  * a manufactured solution (first order in (hx, dt); second order in hv for the
+    x-independent one with dt ~ hv^2);
+  * an exact discrete eigen-solution of the implicit-Euler v-diffusion (to rounding);
+  * a dense space-time brute-force solve of the same scheme on tiny grids, written
+    independently in numpy from the equations of the scheme;
+  * the affine SWR trace map probed column by column: its fixed point equals the
+    single-domain solution, rho(Robin) < rho(Dirichlet) with overlap and
+    rho(Dirichlet) = 1 without overlap (Section 6.3, Section 6.5, Table 1);
+  * the sup-norm contraction of classical SWR on the error equation (Theorem 4.1)
+    and the convergence of the Robin iteration with and without overlap (Theorem 5.1);
+  * the iteration-count trends of Table 1 (qualitative: the schemes differ).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_4596_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Thomas
+# ---------------------------------------------------------------------------
+
+def test_thomas_matches_dense_solve():
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3, 17, 64):
+        a = rng.uniform(-1, 0, n)
+        c = rng.uniform(-1, 0, n)
+        b = 2.5 + rng.uniform(0, 1, n)
+        d = rng.uniform(-1, 1, n)
+        A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        x = oracle.thomas(a, b, c, d)
+        np.testing.assert_allclose(x, np.linalg.solve(A, d), rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Kolmogorov's Gaussian fundamental solution (closed form on R^2)
+# ---------------------------------------------------------------------------
+
+def _kolmogorov_gaussian(x, v, t, mean0, cov0):
+    """Exact solution of u_t + v u_x = u_vv for Gaussian initial data
+    u0 = exp(-1/2 (z-mu0)^T cov0^{-1} (z-mu0)): the law of X' = V, dV = sqrt(2) dW."""
+    A = np.array([[1.0, t], [0.0, 1.0]])
+    Q = np.array([[2 * t ** 3 / 3, t ** 2], [t ** 2, 2 * t]])
+    cov = A @ cov0 @ A.T + Q
+    mu = A @ np.asarray(mean0)
+    inv = np.linalg.inv(cov)
+    X, V = np.meshgrid(x, v, indexing="xy")
+    dx, dv = X - mu[0], V - mu[1]
+    quad = inv[0, 0] * dx * dx + 2 * inv[0, 1] * dx * dv + inv[1, 1] * dv * dv
+    scale = math.sqrt(np.linalg.det(cov0) / np.linalg.det(cov))
+    return scale * np.exp(-0.5 * quad)
+
+
+def _gaussian_problem(nx, nv, T, cfl, nstrips=1, robin=True, p=4.0, overlap=0):
+    v0, v1 = -4.0, 4.0
+    hx = 1.0 / nx
+    dt0 = cfl * hx / 4.0
+    nt = int(math.ceil(T / dt0))
+    dt = T / nt
+    mean0, cov0 = (0.35, 1.0), np.diag([0.05 ** 2, 0.2 ** 2])
+    x = np.arange(nx + 1) * hx
+    v = v0 + np.arange(nv + 1) * ((v1 - v0) / nv)
+    u0 = _kolmogorov_gaussian(x, v, 0.0, mean0, cov0)
+    prob = inputs.Problem(0.0, 1.0, v0, v1, dt, nx, nv, nt, nstrips, overlap, robin,
+                          np.full(max(nstrips - 1, 0), p), np.full(max(nstrips - 1, 0), p),
+                          u0, np.zeros((1, nt + 1)), np.zeros((1, nv + 1, nx + 1)))
+    exact = _kolmogorov_gaussian(x, v, T, mean0, cov0)
+    return prob, exact
+
+
+def test_kolmogorov_gaussian_first_order():
+    """Upwind + implicit Euler converge at first order to the closed form; the error
+    shrinks by ~2 each time hx and dt are halved (hv fine and fixed)."""
+    errs = []
+    for nx in (100, 200, 400):
+        prob, exact = _gaussian_problem(nx, 800, 0.05, 0.8)
+        u = oracle.monolithic(prob)
+        errs.append(np.abs(u - exact).max())
+        # boundary data are zero: the closed form must be negligible there
+        assert np.abs(exact[[0, -1], :]).max() < 1e-13 and np.abs(exact[:, [0, -1]]).max() < 1e-13
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert errs[2] < 0.05, errs
+    assert 1.6 < r1 < 2.4 and 1.6 < r2 < 2.4, (errs, r1, r2)
+
+
+def test_kolmogorov_gaussian_drift_direction_and_mass():
+    """The mean moves by vbar * T in x (transport sign) and the mass is kept."""
+    prob, exact = _gaussian_problem(400, 800, 0.05, 0.8)
+    u = oracle.monolithic(prob)
+    x, v = prob.x_nodes(), prob.v_nodes()
+    mass = u.sum() * prob.hx * prob.hv
+    mass0 = prob.u0.sum() * prob.hx * prob.hv
+    assert abs(mass / mass0 - 1) < 1e-6
+    xbar = (u.sum(axis=0) * x).sum() / u.sum()
+    assert abs(xbar - (0.35 + 1.0 * 0.05)) < 2e-3, xbar
+    vbar = (u.sum(axis=1) * v).sum() / u.sum()
+    assert abs(vbar - 1.0) < 1e-3
+
+
+def test_kolmogorov_gaussian_robin_strips_converge_to_single_domain():
+    prob, _ = _gaussian_problem(64, 256, 0.02, 0.8, nstrips=4, robin=True, p=8.0)
+    mono = oracle.monolithic(prob)
+    res = oracle.swr_solve(prob, 200, 1e-13, 1)
+    assert res["iters"] < 200
+    np.testing.assert_allclose(res["u_T"], mono, rtol=0, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Manufactured solutions
+# ---------------------------------------------------------------------------
+
+def test_manufactured_first_order_in_x_and_t():
+    errs = []
+    for n in (32, 64, 128):
+        prob = inputs.manufactured(nx=n, nv=256, nt=n // 2, T=0.1, nstrips=1, overlap=0)
+        u = oracle.monolithic(prob)
+        X, V = np.meshgrid(prob.x_nodes(), prob.v_nodes())
+        exact = math.exp(-prob.T) * np.sin(math.pi * X) * np.cos(math.pi * V / 2)
+        errs.append(np.abs(u - exact).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.7 < r1 < 2.3 and 1.7 < r2 < 2.3, (errs, r1, r2)
+
+
+def test_x_independent_manufactured_second_order_in_v():
+    """u = exp(-t) cos(pi v / 2): no transport error, f = (pi^2/4 - 1) u; with dt ~ hv^2
+    the error falls by ~4 when hv is halved."""
+    errs = []
+    for nv in (16, 32, 64):
+        hv = 2.0 / nv
+        dt = 0.25 * hv * hv
+        nt = int(round(0.1 / dt))
+        nx = 4
+        x = np.linspace(0, 1, nx + 1)
+        v = -1 + np.arange(nv + 1) * hv
+        X, V = np.meshgrid(x, v)
+        t = np.arange(nt + 1) * dt
+        base = np.cos(math.pi * V / 2)
+        u0 = base.copy()
+        bc_xin = np.zeros((nt + 1, 2, nv + 1))
+        bc_xin[:, 0, :] = np.exp(-t)[:, None] * np.cos(math.pi * v / 2)[None, :]
+        bc_xin[:, 1, :] = bc_xin[:, 0, :]
+        prob = inputs.Problem(0, 1, -1, 1, dt, nx, nv, nt, 1, 0, False, np.zeros(0), np.zeros(0), u0,
+                              np.exp(-t)[None], ((math.pi ** 2 / 4 - 1) * base)[None], bc_xin, None)
+        u = oracle.monolithic(prob)
+        errs.append(np.abs(u - math.exp(-nt * dt) * base).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.4 < r1 < 4.6 and 3.4 < r2 < 4.6, (errs, r1, r2)
+
+
+# ---------------------------------------------------------------------------
+# Exact discrete eigen-solution
+# ---------------------------------------------------------------------------
+
+def _eigen_problem(nx, nv, nt, dt, k, nstrips=1, overlap=0, robin=False, p=4.0):
+    v0, v1 = -1.0, 1.0
+    hv = (v1 - v0) / nv
+    r = dt / hv ** 2
+    i = np.arange(nv + 1)
+    phi = np.sin(k * math.pi * i / nv)
+    phi[0] = phi[-1] = 0.0
+    rho = 1.0 / (1.0 + 4.0 * r * math.sin(k * math.pi * hv / (2 * (v1 - v0))) ** 2)
+    u0 = np.repeat(phi[:, None], nx + 1, axis=1)
+    levels = rho ** np.arange(nt + 1)
+    bc_xin = np.zeros((nt + 1, 2, nv + 1))
+    bc_xin[:, 0, :] = levels[:, None] * phi[None, :]
+    bc_xin[:, 1, :] = bc_xin[:, 0, :]
+    prob = inputs.Problem(0, 1, v0, v1, dt, nx, nv, nt, nstrips, overlap, robin,
+                          np.full(max(nstrips - 1, 0), p), np.full(max(nstrips - 1, 0), p), u0,
+                          np.zeros((1, nt + 1)), np.zeros((1, nv + 1, nx + 1)), bc_xin, None)
+    return prob, levels[-1] * u0
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_eigen_solution_exact_monolithic(k):
+    prob, exact = _eigen_problem(8, 32, 25, 0.004, k)
+    np.testing.assert_allclose(oracle.monolithic(prob), exact, rtol=0, atol=2e-14)
+
+
+@pytest.mark.parametrize("robin,overlap", [(False, 2), (True, 0), (True, 3)])
+def test_eigen_solution_exact_converged_swr(robin, overlap):
+    prob, exact = _eigen_problem(6, 32, 10, 0.004, 3, nstrips=4, overlap=overlap, robin=robin, p=6.0)
+    res = oracle.swr_solve(prob, 400, 1e-15, 0)
+    np.testing.assert_allclose(res["u_T"], exact, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Dense space-time brute force (independent numpy assembly of the same scheme)
+# ---------------------------------------------------------------------------
+
+def _dense_single_domain(prob):
+    """Assemble all time levels of the single-domain scheme as one dense system."""
+    nx, nv, nt = prob.nx, prob.nv, prob.nt
+    N = (nv + 1) * (nx + 1)
+    idx = lambda i, m: i * (nx + 1) + m
+    hx, hv, dt = prob.hx, prob.hv, prob.dt
+    r = dt / hv ** 2
+    v = prob.v_nodes()
+    bc_xin = np.zeros((nt + 1, 2, nv + 1)) if prob.bc_xin is None else prob.bc_xin
+    bc_v = np.zeros((nt + 1, 2, nx + 1)) if prob.bc_v is None else prob.bc_v
+    big = np.zeros((nt * N, nt * N))
+    rhs = np.zeros(nt * N)
+    for n in range(nt):  # equations for level n+1
+        off = n * N
+        for i in range(nv + 1):
+            for m in range(nx + 1):
+                row = off + idx(i, m)
+                big[row, off + idx(i, m)] = 1.0
+                ident = None
+                if i == 0:
+                    ident = bc_v[n + 1, 0, m]
+                elif i == nv:
+                    ident = bc_v[n + 1, 1, m]
+                elif m == 0 and v[i] > 0:
+                    ident = bc_xin[n + 1, 0, i]
+                elif m == nx and v[i] < 0:
+                    ident = bc_xin[n + 1, 1, i]
+                if ident is not None:
+                    rhs[row] = ident
+                    continue
+                # (1 + 2r) u_i - r u_{i-1} - r u_{i+1} - [explicit transport of u^n] = dt f
+                big[row, off + idx(i, m)] = 1 + 2 * r
+                big[row, off + idx(i - 1, m)] = -r
+                big[row, off + idx(i + 1, m)] = -r
+                c = v[i] * dt / hx
+                coeffs = {}
+                if v[i] > 0:
+                    coeffs = {(i, m): 1 - c, (i, m - 1): c}
+                elif v[i] < 0:
+                    coeffs = {(i, m): 1 + c, (i, m + 1): -c}
+                else:
+                    coeffs = {(i, m): 1.0}
+                f = sum(prob.f_time[k, n + 1] * prob.f_space[k, i, m] for k in range(prob.f_time.shape[0]))
+                rhs[row] = dt * f
+                for (ii, mm), w in coeffs.items():
+                    if n == 0:
+                        rhs[row] += w * prob.u0[ii, mm]
+                    else:
+                        big[row, (n - 1) * N + idx(ii, mm)] -= w
+    sol = np.linalg.solve(big, rhs)
+    return sol.reshape(nt, nv + 1, nx + 1)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dense_spacetime_matches_single_domain(seed):
+    prob = inputs.random_data(4, 8, 3, 0.05, 1, 0, False, seed=seed, v_range=(-1.0, 1.25))
+    dense = _dense_single_domain(prob)
+    _, u_all = oracle.monolithic(prob, all_levels=True)
+    np.testing.assert_allclose(u_all[1:], dense, rtol=0, atol=1e-13)
+
+
+def _trace_map(prob):
+    """Affine SWR trace map lambda^k = M lambda^{k-1} + c, probed column by column."""
+    shape = oracle.trace_shape(prob)
+    n = int(np.prod(shape))
+    c, _, _ = oracle.swr_iteration(prob, np.zeros(shape))
+    M = np.zeros((n, n))
+    for e in range(n):
+        unit = np.zeros(n)
+        unit[e] = 1.0
+        out, _, _ = oracle.swr_iteration(prob, unit.reshape(shape))
+        M[:, e] = (out - c).ravel()
+    return M, c.ravel()
+
+
+@pytest.mark.parametrize("robin,overlap", [(False, 2), (True, 0), (True, 2)])
+def test_trace_map_fixed_point_is_single_domain(robin, overlap):
+    prob = inputs.random_data(4, 8, 3, 0.05, 2, overlap, robin, p=3.0, q=5.0, seed=3)
+    M, c = _trace_map(prob)
+    lam_star = np.linalg.solve(np.eye(len(c)) - M, c).reshape(oracle.trace_shape(prob))
+    lam_out, bands, u_T = oracle.swr_iteration(prob, lam_star)
+    np.testing.assert_allclose(lam_out, lam_star, rtol=0, atol=1e-11)
+    dense = _dense_single_domain(prob)
+    np.testing.assert_allclose(u_T, dense[-1], rtol=0, atol=1e-12)
+    # both strips agree on the whole overlap at every time level
+    assert np.abs(bands[:, 0] - bands[:, 1]).max() < 1e-12
+
+
+def test_trace_map_spectral_radii():
+    """Robin converges faster than Dirichlet with overlap; Dirichlet without overlap does
+    not converge (rho = 1), Robin without overlap does (Section 6.5, Table 1)."""
+    def rho(robin, overlap, p=4.0):
+        prob = inputs.random_data(6, 16, 4, 0.04, 2, overlap, robin, p=p, seed=5)
+        M, _ = _trace_map(prob)
+        return np.abs(np.linalg.eigvals(M)).max()
+
+    rho_d2, rho_r2, rho_d0, rho_r0 = rho(False, 2), rho(True, 2), rho(False, 0), rho(True, 0)
+    assert rho_d2 < 1 and rho_r2 < rho_d2, (rho_d2, rho_r2)
+    assert abs(rho_d0 - 1) < 1e-12, rho_d0
+    assert rho_r0 < 1, rho_r0
+
+
+# ---------------------------------------------------------------------------
+# Converged SWR equals the single-domain solution (larger grids)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("robin,overlap,p", [(False, 4, 2.0), (True, 0, 8.0), (True, 2, 8.0)])
+def test_converged_swr_equals_single_domain_manufactured(robin, overlap, p):
+    prob = inputs.manufactured(64, 64, 20, 0.1, nstrips=2, overlap=overlap, robin=robin, p=p)
+    mono = oracle.monolithic(prob)
+    res = oracle.swr_solve(prob, 300, 1e-14, 0)
+    assert res["iters"] < 300
+    np.testing.assert_allclose(res["u_T"], mono, rtol=0, atol=1e-11)
+
+
+def test_converged_swr_equals_single_domain_bumps_many_strips():
+    prob = inputs.gaussian_bumps(48, 64, 30, 2.5e-3, nstrips=4, p=6.0, seed=7)
+    mono = oracle.monolithic(prob)
+    res = oracle.swr_solve(prob, 300, 1e-14, 0)
+    assert res["iters"] < 300
+    np.testing.assert_allclose(res["u_T"], mono, rtol=0, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Convergence behaviour on the error equation (Theorems 4.1 and 5.1)
+# ---------------------------------------------------------------------------
+
+def test_classical_swr_sup_norm_contracts_with_overlap():
+    """Discrete maximum principle: |lambda^k|_inf never grows; with overlap it shrinks."""
+    prob = inputs.error_equation(32, 32, 16, 1 / 32, 2, 3, False, seed=1)
+    lam = prob.lam0.copy()
+    norms = [np.abs(lam).max()]
+    for _ in range(12):
+        lam, _, _ = oracle.swr_iteration(prob, lam)
+        norms.append(np.abs(lam).max())
+    assert all(b <= a * (1 + 1e-14) for a, b in zip(norms, norms[1:])), norms
+    assert norms[-1] < 0.5 * norms[0], norms
+
+
+def test_classical_swr_without_overlap_stagnates():
+    prob = inputs.error_equation(16, 16, 8, 1 / 16, 2, 0, False, seed=2)
+    res = oracle.swr_solve(prob, 20, 0.0, 0)
+    chg = res["hist"][:, 1]
+    assert chg[-1] > 0.5 * chg[1], chg
+
+
+@pytest.mark.parametrize("overlap", [0, 3])
+def test_robin_swr_converges_geometrically(overlap):
+    prob = inputs.error_equation(32, 32, 16, 1 / 32, 2, overlap, True, p=4.0, seed=4)
+    res = oracle.swr_solve(prob, 40, 0.0, 1)
+    mis = res["hist"][:, 0]
+    # contraction measured over two-iteration windows
+    assert all(mis[k + 2] < mis[k] for k in range(len(mis) - 2)), mis
+    assert mis[-1] < 1e-6 * mis[0]
+
+
+def test_robin_needs_fewer_iterations_than_dirichlet():
+    counts = {}
+    for robin, ov, p in [(False, 3, 1.0), (True, 3, 4.0), (True, 0, 4.0)]:
+        prob = inputs.error_equation(32, 32, 16, 1 / 32, 2, ov, robin, p=p, seed=6)
+        counts[(robin, ov)] = oracle.swr_solve(prob, 300, 1e-6, 1)["iters"]
+    assert counts[(True, 3)] < counts[(False, 3)], counts
+    assert counts[(True, 0)] < 300, counts
+
+
+def test_table1_trends():
+    """Table 1 (Section 6.5) on this scheme: the classical count grows under refinement
+    much faster than the optimized one; the paper's own counts are in
+    tests/golden/table1_iteration_counts.txt (they belong to its splitting scheme)."""
+    table = {}
+    with open(os.path.join(GOLDEN, "table1_iteration_counts.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            table[key] = vals
+    assert table["overlap_CSWR"] == ["70", "105", "132", ">150", ">150"]
+    assert [int(x) for x in table["overlap_OSWRp"]] == [9, 12, 15, 17, 18]
+
+    ours = {"cswr": [], "oswr": []}
+    for j, n in enumerate((16, 32, 64)):
+        h = 1.0 / n
+        for name, robin, p in (("cswr", False, 1.0), ("oswr", True, 4.0)):
+            prob = inputs.error_equation(n, 2 * n, n // 2, h, 2, 3, robin, p=p, seed=10 + j)
+            ours[name].append(oracle.swr_solve(prob, 400, 1e-6, 1)["iters"])
+    growth_c = ours["cswr"][-1] / ours["cswr"][0]
+    growth_o = ours["oswr"][-1] / ours["oswr"][0]
+    assert all(o < c for o, c in zip(ours["oswr"], ours["cswr"])), ours
+    assert growth_c > growth_o, ours
+
+
+# ---------------------------------------------------------------------------
+# Validation and norms
+# ---------------------------------------------------------------------------
+
+def test_validation_rejects_bad_descriptors():
+    good = inputs.small_dirichlet()
+    assert oracle.validate(good) == 0
+    assert oracle.validate(good.replace(dt=0.05)) == -2  # CFL = 3.2
+    assert oracle.validate(good.replace(nstrips=3)) == -1  # 3 does not divide 64
+    assert oracle.validate(good.replace(overlap=32)) == -1  # overlap >= cells per strip
+    bad_p = inputs.small_robin()
+    bad_p.p = np.array([0.0])
+    assert oracle.validate(bad_p) == -1
+
+
+def test_strip_layout_of_small_configs():
+    lo, hi = oracle.strip_layout(inputs.small_dirichlet())
+    assert list(lo) == [0, 30] and list(hi) == [34, 64]
+    lo, hi = oracle.strip_layout(inputs.small_robin())
+    assert list(lo) == [0, 32] and list(hi) == [32, 64]
+    lo, hi = oracle.strip_layout(inputs.gaussian_bumps(16, 64, 2, 1e-3, 8, seed=0))
+    assert list(lo) == [0, 8, 16, 24, 32, 40, 48, 56] and list(hi) == [8, 16, 24, 32, 40, 48, 56, 64]
+
+
+def test_interface_norms_by_hand():
+    prob = inputs.error_equation(2, 8, 2, 0.1, 2, 1, False, seed=0)
+    bands = np.zeros(oracle.band_shape(prob))
+    bands[0, 0, 1, 1, 2] = -0.25  # largest mismatch is negative: lower - upper = -0.75
+    bands[0, 1, 1, 1, 2] = 0.5
+    bands[0, 1, 0, 0, 0] = 0.1
+    lam_old = np.zeros(oracle.trace_shape(prob))
+    lam_new = lam_old.copy()
+    lam_new[0, 1, 1, 1] = -0.3
+    e_mis, e_chg, j = oracle.interface_norms(prob, bands, lam_new, lam_old)
+    assert e_mis == 0.75 and e_chg == 0.3
+    assert abs(j - 0.1 * 0.5 * (0.75 ** 2 + 0.1 ** 2)) < 1e-16
+
+
+def test_maximum_principle_nonnegative_data():
+    prob = inputs.gaussian_bumps(32, 64, 40, 2e-3, nstrips=4, p=4.0, seed=9)
+    res = oracle.swr_solve(prob, 3, 0.0, 0)
+    assert res["u_T"].min() > -1e-15
