@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 SWR sweep for the Kolmogorov equation.
+
+Workload (one "step" = one SWR iteration: nt+1 sweep passes over every strip,
+the exchange of the interface data and the interface-error reduction):
+  x in [0,1], v in [-4,4], 2048 x 4096 cells, 8 equal v-strips, Robin p = 4 without
+  overlap, dt = 1e-4, nt = 2000 (CFL 0.8192), forcing = 16 seeded Gaussian bumps plus
+  a Gaussian initial density, zero boundary data, FP64.
+Metric: SWR cell-updates per second (cell-update = one strip node advanced one time
+step in one iteration), higher is better.  Inputs are resident in HBM before the
+timed region; the state of one step (3 x 68 MB) is larger than L2 (129 MB).
+
+Extra keys: "roofline" (sweep kernel: FP64 is bound by the FP64 pipe, FP32 by HBM),
+"cpu_baseline" (the CPU oracle on a bounded sample), "e2e" (through the C ABI from
+pinned host buffers, copies included), "clocks" (nvidia-smi during the timed
+region), "variants" (the FP32 form) and "time_to_tol" (wall time to e_mis < 1e-8).
+
+--impl reference times the CPU oracle (the reference arm of this repository) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SWR cell-updates/s"
+UNIT = "cell-updates/s"
+WORKLOAD = ("SWR at scale: x in [0,1], v in [-4,4], Nx=2048, Nv=4096, 8 v-strips, Robin p=4 "
+            "(no overlap), dt=1e-4, Nt=2000, 16 seeded Gaussian bumps (seed 2)")
+
+# Algorithmic work of one cell-update ("Roofline"):
+FP64_FLOPS_PER_CELL = 8    # 4 fused multiply-adds: transport (2), elimination (1), back-substitution (1)
+BYTES_PER_CELL = {"f64": 24, "f32": 12}  # read y^k, read F, write y^{k+1}
+# FP64 pipe of sm_103a: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(prob, nt_sample: int):
+    """Cell-updates/s of the CPU oracle, single-threaded, on one iteration of the
+    workload restricted to the first nt_sample time steps."""
+    import oracle
+
+    sample = prob.replace(nt=nt_sample)
+    sample.f_time = prob.f_time[:, : nt_sample + 1].copy()
+    from paper_1306_4596_gb300 import swr as swr_mod
+    cells = swr_mod.cell_updates_per_iteration(sample)
+    t0 = time.perf_counter()
+    oracle.swr_iteration(sample, None)
+    dt = time.perf_counter() - t0
+    return cells / dt, cells, dt
+
+
+def run_reference(args, rank: int, world: int):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    from paper_1306_4596_gb300 import inputs, swr as swr_mod
+
+    prob = inputs.at_scale()
+    nt_sample = args.ref_nt
+    sample = prob.replace(nt=nt_sample)
+    sample.f_time = prob.f_time[:, : nt_sample + 1].copy()
+    cells = swr_mod.cell_updates_per_iteration(sample)
+    import oracle
+
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.swr_iteration(sample, None)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.swr_iteration(sample, None)
+    elapsed = time.perf_counter() - t0
+    value = cells * args.steps / elapsed
+    desc = (f"one SWR iteration of the workload over its first {nt_sample} of 2000 time steps "
+            f"({cells} cell-updates) per step; oracle = plain C, FP64, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_iterations(torch, solver, steps: int, warmup: int, dist, world: int, device_index: int):
+    for _ in range(warmup):
+        solver.sweep(1)
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(device_index) as clocks:
+        start.record(stream)
+        solver.sweep(steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, clocks.summary()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30, help="timed SWR iterations")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP32, time-to-tol and CPU legs")
+    ap.add_argument("--cpu-nt", type=int, default=60, help="time steps of the CPU-baseline sample")
+    ap.add_argument("--ref-nt", type=int, default=6, help="time steps per reference-arm step")
+    ap.add_argument("--nt", type=int, default=None,
+                    help="shorter time window (profiling captures only; the JSON line records it)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device_index = torch.cuda.current_device()
+
+    from paper_1306_4596_gb300 import inputs, swr as swr_mod
+
+    swr_mod.load()
+    prob = inputs.at_scale()
+    if args.nt is not None:
+        prob = prob.replace(nt=args.nt)
+        prob.f_time = prob.f_time[:, : args.nt + 1].copy()
+    cells_per_iter = swr_mod.cell_updates_per_iteration(prob)
+
+    # ---- headline: device-resident inputs, profiled sweep ------------------------
+    solver = swr_mod.SWR(prob, args.precision, inputs_on="device", profile=True)
+    ms, clocks = time_iterations(torch, solver, args.steps, args.warmup, dist, world, device_index)
+    st = solver.stats()
+    iters_total = st["iterations"]
+    sweep_ms_per_iter = st["sweep_ms"] / iters_total
+    launches_per_iter = st["launches_per_iter"]
+    pass_launches = prob.nt + 1
+    avg_pass_ms = sweep_ms_per_iter / pass_launches
+    e_hist = solver.error()[3]
+    solver.close()
+
+    value = world * cells_per_iter * args.steps / (ms / 1e3)
+    ms_per_step = ms / args.steps
+    cells_per_pass = cells_per_iter / prob.nt  # every pass advances every strip node once
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    hbm_label = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    if args.precision == "f64":
+        achieved = cells_per_pass * FP64_FLOPS_PER_CELL / (avg_pass_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 4 x 0.5 DFMA/clk x 2 flops x 2.07 GHz",
+                    "kernel": "sweep_pass_kernel<double>", "avg_launch_ms": avg_pass_ms,
+                    "hbm_view": {"achieved_gbs": cells_per_pass * BYTES_PER_CELL["f64"] / (avg_pass_ms / 1e3) / 1e9,
+                                 "peak_gbs": hbm, "peak_source": hbm_label}}
+    else:
+        achieved = cells_per_pass * BYTES_PER_CELL["f32"] / (avg_pass_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "peak_source": hbm_label, "kernel": "sweep_pass_kernel<float>",
+                    "avg_launch_ms": avg_pass_ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.nt is None else WORKLOAD.replace("Nt=2000", f"Nt={args.nt}"),
+                   "cell_updates_per_step": cells_per_iter,
+                   "l2": "state per time step (3 x 68 MB) larger than L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "gpu_launches": launches_per_iter * args.steps,
+        "clocks": clocks,
+        "e_mis_last": float(e_hist[-1, 0]) if len(e_hist) else None,
+    }
+
+    if not args.no_extras and rank == 0:
+        # ---- e2e: host (pinned) buffers through the C ABI, copies included ------------
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with swr_mod.SWR(prob, args.precision, inputs_on="host") as s:
+            s.sweep(args.steps)
+            u_T = s.solution()
+            hist = s.error()[3]
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        h2d = sum(a.nbytes for a in (prob.u0, prob.f_time, prob.f_space) if a is not None)
+        d2h = u_T.nbytes + hist.nbytes
+        line["e2e"] = {"value": cells_per_iter * args.steps / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                       "seconds": e2e_s, "includes": "create (H2D of u0, f) + sweep + solution/history D2H"}
+
+        # ---- the other precision ---------------------------------------------------
+        other = "f32" if args.precision == "f64" else "f64"
+        with swr_mod.SWR(prob, other, inputs_on="device", profile=True) as s:
+            ms2, _ = time_iterations(torch, s, max(args.steps // 3, 3), 1, None, 1, device_index)
+            n2 = max(args.steps // 3, 3)
+            st2 = s.stats()
+        avg2 = st2["sweep_ms"] / st2["iterations"] / pass_launches
+        var = {"dtype": other, "value": cells_per_iter * n2 / (ms2 / 1e3), "unit": UNIT,
+               "avg_pass_ms": avg2}
+        if other == "f32":
+            var["hbm_gbs"] = cells_per_pass * BYTES_PER_CELL["f32"] / (avg2 / 1e3) / 1e9
+            var["hbm_frac"] = var["hbm_gbs"] / hbm
+        line["variants"] = [var]
+
+        # ---- time to e_mis < 1e-8 -----------------------------------------------------
+        ttol = {}
+        for prec in ("f64", "f32"):
+            with swr_mod.SWR(prob, prec, inputs_on="device") as s:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n = s.sweep(60, 1e-8, 1)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                e = s.error()
+            ttol[prec] = {"seconds": el, "iterations": n, "e_mis": e[0], "reached": bool(e[0] < 1e-8)}
+        line["time_to_tol"] = {"tol": 1e-8, "norm": "e_mis", **ttol}
+
+        # ---- CPU oracle on a bounded sample -------------------------------------------
+        rate, cells, secs = cpu_oracle_rate(prob, args.cpu_nt)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one SWR iteration over the first {args.cpu_nt} of 2000 time "
+                                          f"steps ({cells} cell-updates, {secs:.1f} s), plain C FP64 oracle, "
+                                          f"single thread"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * kfp_swr.h -- C ABI of the GB300 (sm_103a) Schwarz waveform relaxation sweep for
+ * the Kolmogorov equation
+ *
+ *     u_t + v u_x - u_vv = f   on (0,T) x [x0,x1] x [v0,v1]
+ *
+ * (the problem of Section 2, eq. "Kolmogorovmain", of Gerardo-Giorda & Tran,
+ * "Parallelizing the Kolmogorov-Fokker-Planck Equation", arXiv:1306.4596), with the
+ * velocity interval split into S strips.  Each iteration solves every strip over
+ * the whole time window from the interface data of the previous iterate (the
+ * parallel form in the Remark after criterion "error" of Section 6.3), using
+ * Dirichlet (classical, eq. "ClassicalSchwarz") or Robin (optimized, eq.
+ * "RobinSchwarz") transmission, then exchanges the interface variables
+ * lambda_1 = Q_1 u_2, lambda_2 = Q_2 u_1 (eq. "lambda12", SWR2 and SWR4) and
+ * measures the mismatch of neighbouring strips on the overlap (eq. "error").
+ *
+ * Discretisation (the paper leaves it open for this problem):
+ *   x_m = x0 + m hx (m = 0..nx), v_i = v0 + i hv (i = 0..nv), t^n = n dt (n = 0..nt);
+ *   explicit first-order upwind transport by the sign of v_i (CFL |v_i| dt/hx <= 1);
+ *   implicit Euler v-diffusion, centred second difference, one tridiagonal system
+ *   per x-column and strip; inflow Dirichlet data at x0 (v_i > 0) and x1 (v_i < 0);
+ *   Dirichlet data at v0 and v1; half-cell finite-volume Robin rows.
+ * Strips: interface j = 0..S-2 has centre node I_j = (j+1) nv/S, overlap nodes
+ * alpha_j = I_j - floor(ov/2) .. beta_j = alpha_j + ov; strip s covers nodes
+ * lo_s = (s ? alpha_{s-1} : 0) .. hi_s = (s < S-1 ? beta_s : nv).
+ *
+ * General conventions
+ *   - Every function returns a kfp_status; no function throws or aborts.  On an
+ *     error the handle (if any) keeps a message readable with kfp_swr_last_error.
+ *   - All GPU work is enqueued on the stream given at create (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  Calls that return host data
+ *     synchronise that stream.
+ *   - The handle owns all device memory it allocates (freed by kfp_swr_destroy).
+ *     Input arrays are copied at create; the caller keeps ownership of them.
+ *   - A handle is not thread-safe: use it from one host thread at a time.
+ *   - Array shapes are row-major, last index fastest, all FP64.
+ */
+#ifndef KFP_SWR_H
+#define KFP_SWR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kfp_swr* kfp_swr_t; /* opaque handle */
+
+typedef enum {
+  KFP_OK = 0,
+  KFP_EINVAL = 1,    /* invalid argument or descriptor */
+  KFP_ECFL = 2,      /* |v_i| dt / hx > 1 somewhere: the explicit upwind step is unstable */
+  KFP_ENOMEM = 3,    /* device or host allocation failed */
+  KFP_ECUDA = 4,     /* a CUDA call failed (message holds the CUDA error string) */
+  KFP_ENOTCONV = 5,  /* max_iters reached before the requested tolerance */
+  KFP_ENUMERIC = 6,  /* a NaN or Inf appeared in the interface norms */
+  KFP_ETIMEOUT = 7,  /* a bounded device-side wait expired */
+  KFP_ENOTSUP = 8    /* the requested mode is not built into this library */
+} kfp_status;
+
+typedef enum { KFP_DIRICHLET = 0, KFP_ROBIN = 1 } kfp_transmission;
+
+/* Arithmetic of the strip solves.  Interface traces, bands, norms and every array
+ * crossing the ABI stay FP64 in all modes. */
+typedef enum { KFP_F64 = 0, KFP_F32 = 1 } kfp_precision;
+
+/* Flags of kfp_swr_desc.flags */
+#define KFP_FLAG_NO_GRAPH 1u  /* launch every kernel directly instead of replaying a CUDA graph */
+#define KFP_FLAG_PROFILE 2u   /* time the sweep, exchange and error kernels with CUDA events */
+
+typedef struct {
+  double x0, x1, v0, v1; /* box [x0,x1] x [v0,v1], x1 > x0, v1 > v0 */
+  double dt;             /* time step, T = nt dt */
+  int nx, nv, nt;        /* intervals in x (>= 1) and v (>= 2), time steps (>= 1) */
+  int nstrips;           /* S >= 1, must divide nv; nv/S >= 2 when S > 1 */
+  int overlap_cells;     /* ov, 0 <= ov < nv/S (ignored when S == 1) */
+  kfp_transmission tc;   /* transmission condition on every interface */
+  const double* p;       /* host [S-1]: Robin p_j > 0 (lower strip's top, p + d/dv); NULL for Dirichlet */
+  const double* q;       /* host [S-1]: Robin q_j > 0 (upper strip's bottom, q - d/dv); NULL = p */
+  kfp_precision prec;    /* arithmetic of the strip solves */
+  unsigned flags;        /* KFP_FLAG_* */
+} kfp_swr_desc;
+
+typedef struct {
+  int on_device;          /* 1: the pointers below are device memory of the current device; 0: host */
+  const double* u0;       /* [nv+1][nx+1] initial data u0(x_m, v_i) (required) */
+  int nforce;             /* number of separable forcing terms R >= 0 */
+  const double* f_time;   /* [R][nt+1] a_r(t^n)       (NULL allowed only when R == 0) */
+  const double* f_space;  /* [R][nv+1][nx+1] F_r(x_m, v_i); f = sum_r a_r(t) F_r(x, v) */
+  const double* bc_xin;   /* [nt+1][2][nv+1] inflow data at x0 ([.][0]) and x1 ([.][1]); NULL = 0 */
+  const double* bc_v;     /* [nt+1][2][nx+1] Dirichlet data at v0 ([.][0]) and v1 ([.][1]); NULL = 0 */
+  const double* lambda0;  /* [S-1][2][nt][nx+1] initial interface data lambda^0; NULL = 0.
+                           * [j][0][n-1] = lambda_1 of interface j at t^n (data at the lower
+                           * strip's top node beta_j), [j][1][n-1] = lambda_2 (data at the
+                           * upper strip's bottom node alpha_j). */
+} kfp_swr_problem;
+
+/*
+ * Create a solver: validate the descriptor (grid, strip layout, CFL, Robin
+ * parameters), build the strip layout and the constant-coefficient tridiagonal
+ * factors (Section 6.3, eq. "Om1_Om2" generalised to S strips), allocate device
+ * memory and copy the inputs (stream-ordered on `cuda_stream`).
+ * Errors: KFP_EINVAL (NULL or inconsistent arguments), KFP_ECFL, KFP_ENOMEM, KFP_ECUDA.
+ * On error *out is set to NULL.
+ */
+kfp_status kfp_swr_create(const kfp_swr_desc* desc, const kfp_swr_problem* prob, void* cuda_stream,
+                          kfp_swr_t* out);
+
+/*
+ * Run SWR iterations (Section 6.3, SWR1-SWR4 in the parallel form of the Remark):
+ * each iteration sweeps every strip over all nt steps from the current interface
+ * data, exchanges the new interface data, and reduces the norms
+ *   e_mis = max over interfaces, n = 1..nt, overlap nodes, m of |u_j - u_{j+1}|  (eq. "error"),
+ *   e_chg = max |lambda^k - lambda^{k-1}|,   j_l2 = dt hx sum (u_j - u_{j+1})^2.
+ * Stops after max_iters iterations or as soon as the norm chosen by tol_kind
+ * (0: e_chg, 1: e_mis) is below tol.  tol <= 0 runs exactly max_iters iterations
+ * without reading anything back in between.  Iterations continue from the current
+ * interface data (calls can be chained).  *iters_done (may be NULL) receives the
+ * number of iterations run by this call.
+ * Errors: KFP_EINVAL, KFP_ECUDA, KFP_ENOTCONV (tol > 0 not reached), KFP_ENUMERIC.
+ */
+kfp_status kfp_swr_sweep(kfp_swr_t h, int max_iters, double tol, int tol_kind, int* iters_done);
+
+/* Copy the current interface data lambda^k of interface `iface` (0..S-2), side 0
+ * (lambda_1, data of the lower strip) or 1 (lambda_2, data of the upper strip):
+ * [nt][nx+1] to dst (host, or device memory when dst_on_device).  Synchronises.
+ * Errors: KFP_EINVAL, KFP_ECUDA. */
+kfp_status kfp_swr_traces(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device);
+
+/* Replace the interface data by src [S-1][2][nt][nx+1] (host or device); used to
+ * resume from a checkpoint taken with kfp_swr_traces.  Errors: KFP_EINVAL, KFP_ECUDA. */
+kfp_status kfp_swr_set_traces(kfp_swr_t h, const double* src, int src_on_device);
+
+/* Norms of the last iteration and the history of all iterations of this handle:
+ * history (may be NULL) receives min(hist_cap, iterations) rows of
+ * (e_mis, e_chg, j_l2).  Any scalar pointer may be NULL.  Synchronises.
+ * Errors: KFP_EINVAL (no iteration has run), KFP_ECUDA. */
+kfp_status kfp_swr_error(kfp_swr_t h, double* e_mis, double* e_chg, double* j_l2, double* history,
+                         int hist_cap);
+
+/* Copy the overlap values of the last iteration, interface `iface`, side 0 (lower
+ * strip) or 1 (upper strip): [nt][ov+1][nx+1], rows alpha_j..beta_j.  Synchronises. */
+kfp_status kfp_swr_bands(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device);
+
+/* Copy the solution at t = T of the last iteration, [nv+1][nx+1]; node i comes from
+ * the lower strip of interface j when i <= I_j and from the upper strip otherwise.
+ * Synchronises.  Errors: KFP_EINVAL (no iteration has run), KFP_ECUDA. */
+kfp_status kfp_swr_solution(kfp_swr_t h, double* dst, int dst_on_device);
+
+/* Counters of this handle (all may be NULL): iterations run, cell-updates per
+ * iteration ((nx+1) * sum_s (hi_s - lo_s + 1) * nt), kernels launched per
+ * iteration, and -- when KFP_FLAG_PROFILE is set -- the summed device time in
+ * milliseconds of the sweep kernels, the exchange kernel and the error kernel
+ * (CUDA events recorded on the handle's stream).  Synchronises. */
+kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_updates_per_iter,
+                         int* launches_per_iter, double* sweep_ms, double* exchange_ms,
+                         double* error_ms);
+
+/* Free every resource of the handle (NULL is ignored).  Synchronises its stream. */
+void kfp_swr_destroy(kfp_swr_t h);
+
+/* Message of the last error on this handle ("" if none); valid until the next call. */
+const char* kfp_swr_last_error(kfp_swr_t h);
+
+/* Message of the last error of a failed kfp_swr_create on this thread. */
+const char* kfp_swr_create_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFP_SWR_H */

@@ -1,0 +1,742 @@
+// kfp_swr.cu -- C ABI (include/kfp_swr.h) and host driver of the GB300 SWR sweep.
+//
+// One handle = one problem resident in HBM.  Per SWR iteration (Section 6.3,
+// SWR1-SWR4 in the parallel form of the Remark) the driver enqueues
+//   nt+1 sweep passes (kfp_kernels.cuh: back-substitution of step k fused with the
+//   elimination of step k+1, all strips and columns at once),
+//   the exchange kernel (new interface data -> current, trace change), and
+//   the error kernel (overlap mismatch e_mis and its squared L2 norm),
+// either as direct launches or as one replayed CUDA graph.
+#include "../../include/kfp_swr.h"
+#include "kfp_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Return a status with the CUDA error text; OBJ is the handle whose message is set.
+#define KFP_CUDA_TRY_ON(OBJ, call)                                                        \
+  do {                                                                                    \
+    cudaError_t e__ = (call);                                                             \
+    if (e__ != cudaSuccess) {                                                             \
+      cudaGetLastError();                                                                 \
+      return (OBJ)->fail(e__ == cudaErrorMemoryAllocation ? KFP_ENOMEM : KFP_ECUDA,       \
+                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__),         \
+                         __FILE__, __LINE__);                                             \
+    }                                                                                     \
+  } while (0)
+#define KFP_CUDA_TRY(call) KFP_CUDA_TRY_ON(this, call)
+#define KFP_CUDA_TRY_H(call) KFP_CUDA_TRY_ON(h, call)
+
+struct Geometry {
+  double x0, x1, v0, v1, dt, hx, hv, r;
+  int nx, nv, nt, S, ov, robin, P, W, Lmax, rows, nforce;
+  std::vector<double> p, q;
+  std::vector<kfp::StripInfo> strips;
+  std::vector<int> row_of;  // [nv+1] row of UT holding node i at t = T
+  long long cells_per_iter;
+};
+
+// ---------------------------------------------------------------------------
+// Validation and strip layout (Section 2 and Section 6.3, eq. "Om1_Om2", for S strips)
+// ---------------------------------------------------------------------------
+
+kfp_status build_geometry(const kfp_swr_desc* d, int nforce, Geometry* g, std::string* err) {
+  auto bad = [&](kfp_status c, const char* m) {
+    *err = m;
+    return c;
+  };
+  if (!d) return bad(KFP_EINVAL, "desc is NULL");
+  if (d->nx < 1 || d->nv < 2 || d->nt < 1 || d->nstrips < 1)
+    return bad(KFP_EINVAL, "need nx >= 1, nv >= 2, nt >= 1, nstrips >= 1");
+  if (!(d->x1 > d->x0) || !(d->v1 > d->v0) || !(d->dt > 0) || !std::isfinite(d->dt))
+    return bad(KFP_EINVAL, "need x1 > x0, v1 > v0, dt > 0");
+  if (d->nv % d->nstrips != 0) return bad(KFP_EINVAL, "nstrips must divide nv");
+  if (d->tc != KFP_DIRICHLET && d->tc != KFP_ROBIN) return bad(KFP_EINVAL, "unknown transmission");
+  if (d->prec != KFP_F64 && d->prec != KFP_F32) return bad(KFP_EINVAL, "unknown precision");
+  if (nforce < 0) return bad(KFP_EINVAL, "nforce < 0");
+  const int S = d->nstrips;
+  const int w = d->nv / S;
+  const int ov = S > 1 ? d->overlap_cells : 0;
+  if (S > 1 && (w < 2 || ov < 0 || ov >= w))
+    return bad(KFP_EINVAL, "need nv/nstrips >= 2 and 0 <= overlap_cells < nv/nstrips");
+  g->p.assign(std::max(S - 1, 0), 0.0);
+  g->q.assign(std::max(S - 1, 0), 0.0);
+  if (S > 1 && d->tc == KFP_ROBIN) {
+    if (!d->p) return bad(KFP_EINVAL, "Robin transmission needs p");
+    for (int j = 0; j < S - 1; ++j) {
+      g->p[j] = d->p[j];
+      g->q[j] = d->q ? d->q[j] : d->p[j];
+      if (!(g->p[j] > 0) || !(g->q[j] > 0) || !std::isfinite(g->p[j]) || !std::isfinite(g->q[j]))
+        return bad(KFP_EINVAL, "Robin parameters must be finite and > 0");
+    }
+  }
+  g->x0 = d->x0; g->x1 = d->x1; g->v0 = d->v0; g->v1 = d->v1; g->dt = d->dt;
+  g->nx = d->nx; g->nv = d->nv; g->nt = d->nt; g->S = S; g->ov = ov;
+  g->robin = (d->tc == KFP_ROBIN) ? 1 : 0;
+  g->nforce = nforce;
+  g->hx = (d->x1 - d->x0) / d->nx;
+  g->hv = (d->v1 - d->v0) / d->nv;
+  g->r = d->dt / (g->hv * g->hv);
+  for (int i = 0; i <= d->nv; ++i) {
+    const double vi = d->v0 + i * g->hv;
+    if (std::fabs(vi) * d->dt / g->hx > 1.0) return bad(KFP_ECFL, "CFL |v| dt / hx > 1");
+  }
+  auto alpha = [&](int j) { return (j + 1) * w - ov / 2; };
+  g->strips.resize(S);
+  int rowoff = 0, Lmax = 0;
+  long long nodes = 0;
+  for (int s = 0; s < S; ++s) {
+    kfp::StripInfo& st = g->strips[s];
+    std::memset(&st, 0, sizeof st);
+    st.lo = s == 0 ? 0 : alpha(s - 1);
+    st.hi = s == S - 1 ? d->nv : alpha(s) + ov;
+    st.L = st.hi - st.lo + 1;
+    st.rowoff = rowoff;
+    st.has_bot = s > 0;
+    st.has_top = s < S - 1;
+    st.alpha_bot = s > 0 ? alpha(s - 1) : 0;
+    st.alpha_top = s < S - 1 ? alpha(s) : 0;
+    if (s < S - 1) { st.p_top = g->p[s]; st.q_top = g->q[s]; }
+    if (s > 0) { st.p_bot = g->p[s - 1]; st.q_bot = g->q[s - 1]; }
+    rowoff += st.L;
+    Lmax = std::max(Lmax, st.L);
+    nodes += st.L;
+  }
+  g->rows = rowoff;
+  g->Lmax = Lmax;
+  g->W = (d->nx + 1 + kfp::kOutCols - 1) / kfp::kOutCols;
+  g->P = ((kfp::kOutCols * g->W + 2) + 31) / 32 * 32;
+  g->cells_per_iter = (long long)(d->nx + 1) * nodes * d->nt;
+  g->row_of.resize(d->nv + 1);
+  for (int i = 0; i <= d->nv; ++i) {
+    int s = 0;
+    while (s < S - 1 && i > (s + 1) * w) ++s;  // lower strip owns i <= I_s
+    g->row_of[i] = g->strips[s].rowoff + (i - g->strips[s].lo);
+  }
+  return KFP_OK;
+}
+
+// Constant-coefficient LU factors of every strip's implicit-Euler system for the
+// three column classes (m = 0, interior, m = nx) and both elimination directions.
+// Layout [S][3][2][3][Lmax]: field 0 = 1/pivot, 1 = coupling to the previously
+// eliminated row, 2 = back-substitution coefficient.
+std::vector<double> build_factors(const Geometry& g) {
+  std::vector<double> coef((size_t)g.S * 3 * 2 * 3 * g.Lmax, 0.0);
+  std::vector<double> a(g.Lmax), b(g.Lmax), c(g.Lmax), cp(g.Lmax);
+  const double r = g.r;
+  for (int s = 0; s < g.S; ++s) {
+    const kfp::StripInfo& st = g.strips[s];
+    const int L = st.L;
+    for (int kappa = 0; kappa < 3; ++kappa) {
+      for (int l = 0; l < L; ++l) {
+        const int i = st.lo + l;
+        const double vi = g.v0 + i * g.hv;
+        const bool inflow = (kappa == 0 && vi > 0) || (kappa == 2 && vi < 0);
+        const bool top = st.has_top && i == st.hi;
+        const bool bot = st.has_bot && i == st.lo;
+        a[l] = 0.0; b[l] = 1.0; c[l] = 0.0;
+        if (i == 0 || i == g.nv || inflow) continue;            // identity rows
+        if (top || bot) {
+          if (!g.robin) continue;                               // Dirichlet: identity
+          if (top) { a[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.p_top * g.dt / g.hv; }
+          else     { c[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.q_bot * g.dt / g.hv; }
+          continue;
+        }
+        a[l] = -r; b[l] = 1 + 2 * r; c[l] = -r;
+      }
+      double* up = &coef[(((size_t)s * 3 + kappa) * 2 + 0) * 3 * g.Lmax];
+      double* dn = &coef[(((size_t)s * 3 + kappa) * 2 + 1) * 3 * g.Lmax];
+      // ascending elimination: y_l = g_l (R_l - a_l y_{l-1}); back: u_l = y_l - cp_l u_{l+1}
+      for (int l = 0; l < L; ++l) {
+        const double piv = b[l] - (l > 0 ? a[l] * cp[l - 1] : 0.0);
+        const double gi = 1.0 / piv;
+        cp[l] = c[l] * gi;
+        up[0 * g.Lmax + l] = gi;
+        up[1 * g.Lmax + l] = a[l];
+        up[2 * g.Lmax + l] = cp[l];
+      }
+      // descending elimination: y_l = g_l (R_l - c_l y_{l+1}); back: u_l = y_l - cp_l u_{l-1}
+      for (int l = L - 1; l >= 0; --l) {
+        const double piv = b[l] - (l < L - 1 ? c[l] * cp[l + 1] : 0.0);
+        const double gi = 1.0 / piv;
+        cp[l] = a[l] * gi;
+        dn[0 * g.Lmax + l] = gi;
+        dn[1 * g.Lmax + l] = c[l];
+        dn[2 * g.Lmax + l] = cp[l];
+      }
+    }
+  }
+  return coef;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+
+struct kfp_swr {
+  Geometry g;
+  kfp_precision prec = KFP_F64;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string last_error;
+
+  // device memory
+  void* Y0 = nullptr;
+  void* Y1 = nullptr;
+  void* UT = nullptr;
+  void* U0 = nullptr;
+  void* F = nullptr;
+  void* coef = nullptr;
+  void* cabs = nullptr;
+  signed char* sgn = nullptr;
+  kfp::StripInfo* strips = nullptr;
+  int* row_of = nullptr;
+  double* dta = nullptr;
+  double* bc_xin = nullptr;
+  double* bc_v = nullptr;
+  double* lam_in = nullptr;
+  double* lam_next = nullptr;
+  double* bands = nullptr;
+  double* partial = nullptr;   // 2 doubles per reduction block
+  unsigned* tickets = nullptr; // [2]
+  double* scal = nullptr;      // [3] e_mis, e_chg, j_l2
+  double* hist = nullptr;      // [hist_cap][3]
+  int* iter = nullptr;         // device iteration counter (history slot)
+  double* stage = nullptr;     // [nv+1][nx+1] solution staging
+  double* host_scal = nullptr; // pinned [3]
+  int hist_cap = 0;
+  int reduce_blocks = 0;
+
+  size_t n_trace = 0, n_band = 0, band_per_side = 0;
+  long long iterations = 0;
+  std::vector<double> history;  // host copy, 3 per iteration
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double t_sweep = 0, t_exchange = 0, t_error = 0;
+
+  kfp_status fail(kfp_status c, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    last_error = buf;
+    return c;
+  }
+
+  size_t elem() const { return prec == KFP_F64 ? sizeof(double) : sizeof(float); }
+  int launches_per_iter() const { return g.nt + 1 + 2; }
+
+  template <typename T>
+  kfp::PassArgs<T> pass_args() const {
+    kfp::PassArgs<T> A;
+    A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.S = g.S; A.ov = g.ov; A.P = g.P; A.W = g.W;
+    A.Lmax = g.Lmax; A.nforce = g.nforce; A.robin = g.robin;
+    A.two_dt_hv = 2.0 * g.dt / g.hv;
+    A.inv_2hv = 1.0 / (2.0 * g.hv);
+    A.strips = strips;
+    A.coef = (const T*)coef;
+    A.cabs = (const T*)cabs;
+    A.sgn = sgn;
+    A.U0 = (const T*)U0;
+    A.F = (const T*)F;
+    A.dta = dta;
+    A.bc_xin = bc_xin;
+    A.bc_v = bc_v;
+    A.lam_in = lam_in;
+    A.lam_next = lam_next;
+    A.bands = bands;
+    A.Y0 = (T*)Y0;
+    A.Y1 = (T*)Y1;
+    A.UT = (T*)UT;
+    return A;
+  }
+
+  template <typename T>
+  void enqueue_passes(cudaStream_t st) const {
+    const kfp::PassArgs<T> A = pass_args<T>();
+    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
+    const dim3 block(kfp::kWarpsPerBlock * 32);
+    // pass k runs in ascending row order when k is even (step 1 is factored upward)
+    kfp::sweep_pass_kernel<T, true, 0><<<grid, block, 0, st>>>(A, 0);
+    for (int k = 1; k < g.nt; ++k) {
+      if (k & 1) kfp::sweep_pass_kernel<T, false, 1><<<grid, block, 0, st>>>(A, k);
+      else       kfp::sweep_pass_kernel<T, true, 1><<<grid, block, 0, st>>>(A, k);
+    }
+    if (g.nt & 1) kfp::sweep_pass_kernel<T, false, 2><<<grid, block, 0, st>>>(A, g.nt);
+    else          kfp::sweep_pass_kernel<T, true, 2><<<grid, block, 0, st>>>(A, g.nt);
+  }
+
+  void record(int idx, cudaStream_t st, bool capturing) const {
+    if (!(flags & KFP_FLAG_PROFILE)) return;
+    if (capturing) cudaEventRecordWithFlags(ev[idx], st, cudaEventRecordExternal);
+    else cudaEventRecord(ev[idx], st);
+  }
+
+  // One SWR iteration: sweep, exchange, error.
+  void enqueue_iteration(cudaStream_t st, bool capturing) const {
+    record(0, st, capturing);
+    if (prec == KFP_F64) enqueue_passes<double>(st);
+    else enqueue_passes<float>(st);
+    record(1, st, capturing);
+    if (g.S > 1) {
+      kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+          lam_next, lam_in, n_trace, partial, tickets + 0, scal);
+    }
+    record(2, st, capturing);
+    if (g.S > 1) {
+      kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+          bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
+          scal, hist, iter, hist_cap);
+    }
+    record(3, st, capturing);
+  }
+
+  kfp_status build_graph() {
+    if (graph_exec) return KFP_OK;
+    if (!cap_stream) KFP_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    KFP_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(cap_stream, true);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap_stream, &gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KFP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    graph = gr;
+    KFP_CUDA_TRY(cudaGraphInstantiate(&graph_exec, graph, 0));
+    return KFP_OK;
+  }
+
+  void drop_graph() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    graph_exec = nullptr;
+    graph = nullptr;
+  }
+
+  kfp_status ensure_history(int n) {
+    if (n <= hist_cap) return KFP_OK;
+    int cap = std::max(n, 64);
+    double* h = nullptr;
+    KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+    KFP_CUDA_TRY(cudaMalloc(&h, sizeof(double) * 3 * (size_t)cap));
+    if (hist) cudaFree(hist);
+    hist = h;
+    hist_cap = cap;
+    drop_graph();  // the graph captured the old pointer
+    return KFP_OK;
+  }
+
+  kfp_status sweep(int max_iters, double tol, int tol_kind, int* iters_done) {
+    if (iters_done) *iters_done = 0;
+    if (max_iters < 0 || (tol_kind != 0 && tol_kind != 1))
+      return fail(KFP_EINVAL, "need max_iters >= 0 and tol_kind in {0, 1}");
+    if (max_iters == 0) return KFP_OK;
+    kfp_status rc = ensure_history(max_iters);
+    if (rc) return rc;
+    KFP_CUDA_TRY(cudaMemsetAsync(iter, 0, sizeof(int), stream));
+    const bool use_graph = !(flags & KFP_FLAG_NO_GRAPH);
+    if (use_graph) {
+      rc = build_graph();
+      if (rc) return rc;
+    }
+    const bool check = tol > 0;
+    const bool profile = (flags & KFP_FLAG_PROFILE) != 0;
+    int done = 0;
+    bool converged = false;
+    for (int it = 0; it < max_iters; ++it) {
+      if (use_graph) {
+        KFP_CUDA_TRY(cudaGraphLaunch(graph_exec, stream));
+      } else {
+        enqueue_iteration(stream, false);
+        KFP_CUDA_TRY(cudaGetLastError());
+      }
+      ++done;
+      if (profile) {
+        KFP_CUDA_TRY(cudaEventSynchronize(ev[3]));
+        float a = 0, b = 0, c = 0;
+        KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
+        t_sweep += a; t_exchange += b; t_error += c;
+      }
+      if (check && g.S > 1) {
+        KFP_CUDA_TRY(cudaMemcpyAsync(host_scal, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, stream));
+        KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+        const double v = tol_kind == 0 ? host_scal[1] : host_scal[0];
+        if (!std::isfinite(host_scal[0]) || !std::isfinite(host_scal[1]) || !std::isfinite(host_scal[2])) {
+          rc = fail(KFP_ENUMERIC, "non-finite interface norm at iteration %lld", iterations + done);
+          break;
+        }
+        if (v < tol) { converged = true; break; }
+      }
+    }
+    // pull this call's history
+    if (g.S > 1) {
+      std::vector<double> h((size_t)3 * done);
+      KFP_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * (size_t)std::min(done, hist_cap),
+                                   cudaMemcpyDeviceToHost, stream));
+      KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+      history.insert(history.end(), h.begin(), h.end());
+    } else {
+      KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+      history.insert(history.end(), (size_t)3 * done, 0.0);
+    }
+    KFP_CUDA_TRY(cudaGetLastError());
+    iterations += done;
+    if (iters_done) *iters_done = done;
+    if (rc) return rc;
+    if (g.S > 1) {
+      const double* last = &history[history.size() - 3];
+      if (!std::isfinite(last[0]) || !std::isfinite(last[1]) || !std::isfinite(last[2]))
+        return fail(KFP_ENUMERIC, "non-finite interface norm");
+    }
+    if (check && g.S > 1 && !converged)
+      return fail(KFP_ENOTCONV, "tolerance %g not reached in %d iterations", tol, done);
+    return KFP_OK;
+  }
+
+  void release() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    void* bufs[] = {Y0, Y1, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
+                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage};
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+    if (host_scal) cudaFreeHost(host_scal);
+  }
+};
+
+namespace {
+
+// Copy a caller FP64 array [rows][nx+1] into a padded device array [rows][P] of T.
+kfp_status upload_padded(kfp_swr* h, const double* src, int rows, int on_device, void* dst) {
+  const Geometry& g = h->g;
+  const size_t n = (size_t)rows * (g.nx + 1);
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(double) * n, h->stream);
+  if (e != cudaSuccess) return h->fail(KFP_ENOMEM, "staging allocation failed");
+  e = cudaMemcpyAsync(tmp, src, sizeof(double) * n,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    if (h->prec == KFP_F64)
+      kfp::pad_rows_kernel<double><<<blocks, 256, 0, h->stream>>>(tmp, rows, g.nx, g.P, (double*)dst);
+    else
+      kfp::pad_rows_kernel<float><<<blocks, 256, 0, h->stream>>>(tmp, rows, g.nx, g.P, (float*)dst);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(tmp, h->stream);
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "upload failed: %s", cudaGetErrorString(e));
+  return KFP_OK;
+}
+
+kfp_status alloc(kfp_swr* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(KFP_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return KFP_OK;
+}
+
+kfp_status copy_in(kfp_swr* h, void* dst, const void* src, size_t bytes, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "copy failed: %s", cudaGetErrorString(e));
+  return KFP_OK;
+}
+
+kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem* pb) {
+  Geometry& g = h->g;
+  const size_t es = h->elem();
+  const size_t nxp = g.nx + 1;
+  kfp_status rc;
+#define TRY(x)            \
+  do {                    \
+    rc = (x);             \
+    if (rc) return rc;    \
+  } while (0)
+  // state buffers
+  const size_t ystate = (size_t)g.rows * g.P * es;
+  TRY(alloc(h, &h->Y0, ystate));
+  TRY(alloc(h, &h->Y1, ystate));
+  TRY(alloc(h, &h->UT, ystate));
+  TRY(alloc(h, &h->U0, (size_t)(g.nv + 1) * g.P * es));
+  TRY(alloc(h, &h->F, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es));
+  cudaMemsetAsync(h->Y0, 0, ystate, h->stream);
+  cudaMemsetAsync(h->Y1, 0, ystate, h->stream);
+  cudaMemsetAsync(h->UT, 0, ystate, h->stream);
+  cudaMemsetAsync(h->U0, 0, (size_t)(g.nv + 1) * g.P * es, h->stream);
+  cudaMemsetAsync(h->F, 0, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es, h->stream);
+  TRY(upload_padded(h, pb->u0, g.nv + 1, pb->on_device, h->U0));
+  for (int r = 0; r < g.nforce; ++r)
+    TRY(upload_padded(h, pb->f_space + (size_t)r * (g.nv + 1) * nxp, g.nv + 1, pb->on_device,
+                      (char*)h->F + (size_t)r * (g.nv + 1) * g.P * es));
+
+  // dt * a_r(t^n), [nt+1][nforce]
+  {
+    std::vector<double> fa((size_t)std::max(g.nforce, 1) * (g.nt + 1), 0.0);
+    if (g.nforce > 0) {
+      std::vector<double> ft((size_t)g.nforce * (g.nt + 1));
+      if (pb->on_device) {
+        if (cudaMemcpy(ft.data(), pb->f_time, sizeof(double) * ft.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return h->fail(KFP_ECUDA, "reading f_time failed");
+      } else {
+        std::memcpy(ft.data(), pb->f_time, sizeof(double) * ft.size());
+      }
+      for (int n = 0; n <= g.nt; ++n)
+        for (int r = 0; r < g.nforce; ++r)
+          fa[(size_t)n * g.nforce + r] = g.dt * ft[(size_t)r * (g.nt + 1) + n];
+    }
+    TRY(alloc(h, (void**)&h->dta, sizeof(double) * fa.size()));
+    KFP_CUDA_TRY_H(cudaMemcpy(h->dta, fa.data(), sizeof(double) * fa.size(), cudaMemcpyHostToDevice));
+  }
+
+  // per-row tables and factors
+  {
+    std::vector<double> cabs(g.nv + 1);
+    std::vector<signed char> sgn(g.nv + 1);
+    for (int i = 0; i <= g.nv; ++i) {
+      const double vi = g.v0 + i * g.hv;
+      cabs[i] = std::fabs(vi * g.dt / g.hx);
+      sgn[i] = vi > 0 ? 1 : (vi < 0 ? -1 : 0);
+    }
+    std::vector<double> coef = build_factors(g);
+    TRY(alloc(h, &h->cabs, (g.nv + 1) * es));
+    TRY(alloc(h, &h->coef, coef.size() * es));
+    if (h->prec == KFP_F64) {
+      KFP_CUDA_TRY_H(cudaMemcpy(h->cabs, cabs.data(), sizeof(double) * cabs.size(), cudaMemcpyHostToDevice));
+      KFP_CUDA_TRY_H(cudaMemcpy(h->coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> c32(cabs.begin(), cabs.end()), f32(coef.begin(), coef.end());
+      KFP_CUDA_TRY_H(cudaMemcpy(h->cabs, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice));
+      KFP_CUDA_TRY_H(cudaMemcpy(h->coef, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice));
+    }
+    TRY(alloc(h, (void**)&h->sgn, sgn.size()));
+    KFP_CUDA_TRY_H(cudaMemcpy(h->sgn, sgn.data(), sgn.size(), cudaMemcpyHostToDevice));
+    TRY(alloc(h, (void**)&h->strips, sizeof(kfp::StripInfo) * g.S));
+    KFP_CUDA_TRY_H(cudaMemcpy(h->strips, g.strips.data(), sizeof(kfp::StripInfo) * g.S, cudaMemcpyHostToDevice));
+    TRY(alloc(h, (void**)&h->row_of, sizeof(int) * (g.nv + 1)));
+    KFP_CUDA_TRY_H(cudaMemcpy(h->row_of, g.row_of.data(), sizeof(int) * (g.nv + 1), cudaMemcpyHostToDevice));
+  }
+
+  // boundary data
+  if (pb->bc_xin) {
+    const size_t n = (size_t)(g.nt + 1) * 2 * (g.nv + 1);
+    TRY(alloc(h, (void**)&h->bc_xin, sizeof(double) * n));
+    TRY(copy_in(h, h->bc_xin, pb->bc_xin, sizeof(double) * n, pb->on_device));
+  }
+  if (pb->bc_v) {
+    const size_t n = (size_t)(g.nt + 1) * 2 * nxp;
+    TRY(alloc(h, (void**)&h->bc_v, sizeof(double) * n));
+    TRY(copy_in(h, h->bc_v, pb->bc_v, sizeof(double) * n, pb->on_device));
+  }
+
+  // interface data, overlaps, reductions
+  const int nif = std::max(g.S - 1, 0);
+  h->n_trace = (size_t)nif * 2 * g.nt * nxp;
+  h->band_per_side = (size_t)g.nt * (g.ov + 1) * nxp;
+  h->n_band = (size_t)nif * 2 * h->band_per_side;
+  TRY(alloc(h, (void**)&h->lam_in, sizeof(double) * h->n_trace));
+  TRY(alloc(h, (void**)&h->lam_next, sizeof(double) * h->n_trace));
+  TRY(alloc(h, (void**)&h->bands, sizeof(double) * h->n_band));
+  cudaMemsetAsync(h->lam_next, 0, sizeof(double) * h->n_trace, h->stream);
+  cudaMemsetAsync(h->bands, 0, sizeof(double) * h->n_band, h->stream);
+  if (pb->lambda0) TRY(copy_in(h, h->lam_in, pb->lambda0, sizeof(double) * h->n_trace, pb->on_device));
+  else cudaMemsetAsync(h->lam_in, 0, sizeof(double) * h->n_trace, h->stream);
+
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  h->device = dev;
+  h->reduce_blocks = std::max(sms, 1) * 4;
+  TRY(alloc(h, (void**)&h->partial, sizeof(double) * 4 * h->reduce_blocks));
+  TRY(alloc(h, (void**)&h->tickets, sizeof(unsigned) * 2));
+  TRY(alloc(h, (void**)&h->scal, sizeof(double) * 3));
+  TRY(alloc(h, (void**)&h->iter, sizeof(int)));
+  TRY(alloc(h, (void**)&h->stage, sizeof(double) * (g.nv + 1) * nxp));
+  cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * 2, h->stream);
+  cudaMemsetAsync(h->scal, 0, sizeof(double) * 3, h->stream);
+  cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream);
+  KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->host_scal, sizeof(double) * 3));
+  for (auto& e : h->ev) KFP_CUDA_TRY_H(cudaEventCreate(&e));
+  KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
+  KFP_CUDA_TRY_H(cudaGetLastError());
+  return KFP_OK;
+#undef TRY
+}
+
+kfp_status copy_out(kfp_swr* h, double* dst, const double* src, size_t n, int dst_on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * n,
+                                  dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "copy out failed: %s", cudaGetErrorString(e));
+  return KFP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+kfp_status kfp_swr_create(const kfp_swr_desc* desc, const kfp_swr_problem* prob, void* cuda_stream,
+                          kfp_swr_t* out) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return KFP_EINVAL;
+  }
+  *out = nullptr;
+  if (!desc || !prob || !prob->u0) {
+    g_create_error = "desc, prob and prob->u0 are required";
+    return KFP_EINVAL;
+  }
+  if (prob->nforce > 0 && (!prob->f_time || !prob->f_space)) {
+    g_create_error = "nforce > 0 needs f_time and f_space";
+    return KFP_EINVAL;
+  }
+  kfp_swr* h = new (std::nothrow) kfp_swr();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return KFP_ENOMEM;
+  }
+  std::string err;
+  kfp_status rc = build_geometry(desc, prob->nforce, &h->g, &err);
+  if (rc) {
+    g_create_error = err;
+    delete h;
+    return rc;
+  }
+  h->prec = desc->prec;
+  h->flags = desc->flags;
+  h->stream = (cudaStream_t)cuda_stream;
+  rc = create_impl(h, desc, prob);
+  if (rc) {
+    g_create_error = h->last_error;
+    cudaStreamSynchronize(h->stream);
+    h->release();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return KFP_OK;
+}
+
+kfp_status kfp_swr_sweep(kfp_swr_t h, int max_iters, double tol, int tol_kind, int* iters_done) {
+  if (!h) return KFP_EINVAL;
+  h->last_error.clear();
+  return h->sweep(max_iters, tol, tol_kind, iters_done);
+}
+
+kfp_status kfp_swr_traces(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device) {
+  if (!h) return KFP_EINVAL;
+  if (!dst || iface < 0 || iface >= h->g.S - 1 || side < 0 || side > 1)
+    return h->fail(KFP_EINVAL, "need 0 <= iface < nstrips-1, side in {0,1}, dst != NULL");
+  const size_t n = (size_t)h->g.nt * (h->g.nx + 1);
+  return copy_out(h, dst, h->lam_in + ((size_t)iface * 2 + side) * n, n, dst_on_device);
+}
+
+kfp_status kfp_swr_set_traces(kfp_swr_t h, const double* src, int src_on_device) {
+  if (!h) return KFP_EINVAL;
+  if (!src) return h->fail(KFP_EINVAL, "src is NULL");
+  if (h->n_trace == 0) return KFP_OK;
+  kfp_status rc = copy_in(h, h->lam_in, src, sizeof(double) * h->n_trace, src_on_device);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(KFP_ECUDA, "sync failed");
+  return KFP_OK;
+}
+
+kfp_status kfp_swr_error(kfp_swr_t h, double* e_mis, double* e_chg, double* j_l2, double* history,
+                         int hist_cap) {
+  if (!h) return KFP_EINVAL;
+  if (h->iterations == 0) return h->fail(KFP_EINVAL, "no iteration has run");
+  const double* last = &h->history[h->history.size() - 3];
+  if (e_mis) *e_mis = last[0];
+  if (e_chg) *e_chg = last[1];
+  if (j_l2) *j_l2 = last[2];
+  if (history && hist_cap > 0) {
+    const size_t rows = std::min<size_t>((size_t)hist_cap, h->history.size() / 3);
+    std::memcpy(history, h->history.data(), sizeof(double) * 3 * rows);
+  }
+  return KFP_OK;
+}
+
+kfp_status kfp_swr_bands(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device) {
+  if (!h) return KFP_EINVAL;
+  if (!dst || iface < 0 || iface >= h->g.S - 1 || side < 0 || side > 1)
+    return h->fail(KFP_EINVAL, "need 0 <= iface < nstrips-1, side in {0,1}, dst != NULL");
+  return copy_out(h, dst, h->bands + ((size_t)iface * 2 + side) * h->band_per_side,
+                  h->band_per_side, dst_on_device);
+}
+
+kfp_status kfp_swr_solution(kfp_swr_t h, double* dst, int dst_on_device) {
+  if (!h) return KFP_EINVAL;
+  if (!dst) return h->fail(KFP_EINVAL, "dst is NULL");
+  if (h->iterations == 0) return h->fail(KFP_EINVAL, "no iteration has run");
+  const Geometry& g = h->g;
+  const size_t n = (size_t)(g.nv + 1) * (g.nx + 1);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  if (h->prec == KFP_F64)
+    kfp::gather_solution_kernel<double><<<blocks, 256, 0, h->stream>>>((const double*)h->UT, h->row_of,
+                                                                      g.nv, g.nx, g.P, h->stage);
+  else
+    kfp::gather_solution_kernel<float><<<blocks, 256, 0, h->stream>>>((const float*)h->UT, h->row_of,
+                                                                     g.nv, g.nx, g.P, h->stage);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "gather failed: %s", cudaGetErrorString(e));
+  return copy_out(h, dst, h->stage, n, dst_on_device);
+}
+
+kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_updates_per_iter,
+                         int* launches_per_iter, double* sweep_ms, double* exchange_ms,
+                         double* error_ms) {
+  if (!h) return KFP_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(KFP_ECUDA, "sync failed");
+  if (iterations) *iterations = h->iterations;
+  if (cell_updates_per_iter) *cell_updates_per_iter = h->g.cells_per_iter;
+  if (launches_per_iter) *launches_per_iter = h->g.S > 1 ? h->launches_per_iter() : h->g.nt + 1;
+  if (sweep_ms) *sweep_ms = h->t_sweep;
+  if (exchange_ms) *exchange_ms = h->t_exchange;
+  if (error_ms) *error_ms = h->t_error;
+  return KFP_OK;
+}
+
+void kfp_swr_destroy(kfp_swr_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  h->release();
+  delete h;
+}
+
+const char* kfp_swr_last_error(kfp_swr_t h) { return h ? h->last_error.c_str() : ""; }
+
+const char* kfp_swr_create_error(void) { return g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in ``include/kfp_swr.h`` (argument marshalling only).
+
+The functions ``kfp_swr_create`` ... ``kfp_swr_destroy`` carry the C names and
+arguments one to one; every step of the method runs in the CUDA library.  PyTorch
+is used for device memory and for the stream handle only.  There is no CPU
+fallback: if ``libkfp_swr.so`` cannot be built or loaded, every call raises.
+
+``SWR`` is a small convenience wrapper that takes an ``inputs.Problem``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+KFP_OK, KFP_EINVAL, KFP_ECFL, KFP_ENOMEM, KFP_ECUDA, KFP_ENOTCONV, KFP_ENUMERIC, KFP_ETIMEOUT, KFP_ENOTSUP = range(9)
+STATUS_NAMES = {0: "KFP_OK", 1: "KFP_EINVAL", 2: "KFP_ECFL", 3: "KFP_ENOMEM", 4: "KFP_ECUDA",
+                5: "KFP_ENOTCONV", 6: "KFP_ENUMERIC", 7: "KFP_ETIMEOUT", 8: "KFP_ENOTSUP"}
+KFP_DIRICHLET, KFP_ROBIN = 0, 1
+KFP_F64, KFP_F32 = 0, 1
+KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE = 1, 2
+
+EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
+            "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
+            "kfp_swr_last_error", "kfp_swr_create_error")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class kfp_swr_desc(ctypes.Structure):
+    _fields_ = [
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("v0", ctypes.c_double), ("v1", ctypes.c_double),
+        ("dt", ctypes.c_double), ("nx", ctypes.c_int), ("nv", ctypes.c_int), ("nt", ctypes.c_int),
+        ("nstrips", ctypes.c_int), ("overlap_cells", ctypes.c_int), ("tc", ctypes.c_int),
+        ("p", ctypes.c_void_p), ("q", ctypes.c_void_p), ("prec", ctypes.c_int), ("flags", ctypes.c_uint),
+    ]
+
+
+class kfp_swr_problem(ctypes.Structure):
+    _fields_ = [
+        ("on_device", ctypes.c_int), ("u0", ctypes.c_void_p), ("nforce", ctypes.c_int),
+        ("f_time", ctypes.c_void_p), ("f_space", ctypes.c_void_p), ("bc_xin", ctypes.c_void_p),
+        ("bc_v", ctypes.c_void_p), ("lambda0", ctypes.c_void_p),
+    ]
+
+
+class KfpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(rebuild: bool = False):
+    """Build (if stale) and load ``libkfp_swr.so``; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None or rebuild:
+            path = _build.build(force=rebuild)
+            lib = ctypes.CDLL(path)
+            vp, ip, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int
+            llp = ctypes.POINTER(ctypes.c_longlong)
+            lib.kfp_swr_create.argtypes = [ctypes.POINTER(kfp_swr_desc), ctypes.POINTER(kfp_swr_problem), vp,
+                                           ctypes.POINTER(vp)]
+            lib.kfp_swr_sweep.argtypes = [vp, i, ctypes.c_double, i, ip]
+            lib.kfp_swr_traces.argtypes = [vp, i, i, vp, i]
+            lib.kfp_swr_set_traces.argtypes = [vp, vp, i]
+            lib.kfp_swr_error.argtypes = [vp, _dp, _dp, _dp, _dp, i]
+            lib.kfp_swr_bands.argtypes = [vp, i, i, vp, i]
+            lib.kfp_swr_solution.argtypes = [vp, vp, i]
+            lib.kfp_swr_stats.argtypes = [vp, llp, llp, ip, _dp, _dp, _dp]
+            lib.kfp_swr_destroy.argtypes = [vp]
+            lib.kfp_swr_destroy.restype = None
+            lib.kfp_swr_last_error.argtypes = [vp]
+            lib.kfp_swr_last_error.restype = ctypes.c_char_p
+            lib.kfp_swr_create_error.argtypes = []
+            lib.kfp_swr_create_error.restype = ctypes.c_char_p
+            for name in ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces",
+                         "kfp_swr_error", "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats"):
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(h, status: int, allow=()):
+    if status != KFP_OK and status not in allow:
+        msg = _lib.kfp_swr_last_error(h).decode() if h else _lib.kfp_swr_create_error().decode()
+        raise KfpError(status, msg)
+    return status
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names and arguments
+# ---------------------------------------------------------------------------
+
+def kfp_swr_create(desc: kfp_swr_desc, prob: kfp_swr_problem, cuda_stream: int = 0) -> int:
+    lib = load()
+    out = ctypes.c_void_p()
+    st = lib.kfp_swr_create(ctypes.byref(desc), ctypes.byref(prob), ctypes.c_void_p(cuda_stream), ctypes.byref(out))
+    _check(None, st)
+    return out.value
+
+
+def kfp_swr_sweep(h: int, max_iters: int, tol: float = 0.0, tol_kind: int = 0, allow_notconv: bool = False) -> int:
+    done = ctypes.c_int()
+    st = load().kfp_swr_sweep(h, max_iters, tol, tol_kind, ctypes.byref(done))
+    _check(h, st, allow=(KFP_ENOTCONV,) if allow_notconv else ())
+    return done.value
+
+
+def kfp_swr_traces(h: int, iface: int, side: int, dst_ptr: int, dst_on_device: int) -> None:
+    _check(h, load().kfp_swr_traces(h, iface, side, dst_ptr, dst_on_device))
+
+
+def kfp_swr_set_traces(h: int, src_ptr: int, src_on_device: int) -> None:
+    _check(h, load().kfp_swr_set_traces(h, src_ptr, src_on_device))
+
+
+def kfp_swr_error(h: int, hist_cap: int = 0):
+    e = (ctypes.c_double(), ctypes.c_double(), ctypes.c_double())
+    hist = np.zeros((max(hist_cap, 1), 3))
+    _check(h, load().kfp_swr_error(h, *[ctypes.byref(x) for x in e],
+                                   hist.ctypes.data_as(_dp) if hist_cap > 0 else None, hist_cap))
+    return e[0].value, e[1].value, e[2].value, hist[:hist_cap]
+
+
+def kfp_swr_bands(h: int, iface: int, side: int, dst_ptr: int, dst_on_device: int) -> None:
+    _check(h, load().kfp_swr_bands(h, iface, side, dst_ptr, dst_on_device))
+
+
+def kfp_swr_solution(h: int, dst_ptr: int, dst_on_device: int) -> None:
+    _check(h, load().kfp_swr_solution(h, dst_ptr, dst_on_device))
+
+
+def kfp_swr_stats(h: int) -> dict:
+    it, cells = ctypes.c_longlong(), ctypes.c_longlong()
+    launches = ctypes.c_int()
+    t = (ctypes.c_double(), ctypes.c_double(), ctypes.c_double())
+    _check(h, load().kfp_swr_stats(h, ctypes.byref(it), ctypes.byref(cells), ctypes.byref(launches),
+                                   *[ctypes.byref(x) for x in t]))
+    return {"iterations": it.value, "cell_updates_per_iter": cells.value, "launches_per_iter": launches.value,
+            "sweep_ms": t[0].value, "exchange_ms": t[1].value, "error_ms": t[2].value}
+
+
+def kfp_swr_destroy(h: int) -> None:
+    if h:
+        load().kfp_swr_destroy(h)
+
+
+def kfp_swr_last_error(h: int) -> str:
+    return load().kfp_swr_last_error(h).decode()
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+def cell_updates_per_iteration(prob) -> int:
+    """Strip nodes advanced per iteration: (nx+1) * sum_s (hi_s - lo_s + 1) * nt."""
+    S, w, ov = prob.nstrips, prob.nv // prob.nstrips, (prob.overlap if prob.nstrips > 1 else 0)
+    nodes = 0
+    for s in range(S):
+        lo = 0 if s == 0 else s * w - ov // 2
+        hi = prob.nv if s == S - 1 else (s + 1) * w - ov // 2 + ov
+        nodes += hi - lo + 1
+    return (prob.nx + 1) * nodes * prob.nt
+
+
+class SWR:
+    """One problem resident on the current CUDA device.
+
+    ``inputs_on`` = "device": the problem arrays are first copied into torch CUDA
+    tensors and handed over as device pointers; "host": host (pinned) pointers are
+    handed over and the library copies them in."""
+
+    def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
+                 graph: bool = True, profile: bool = False):
+        import torch
+
+        self.prob = prob
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        S = prob.nstrips
+        self._keep = []
+        on_dev = inputs_on == "device"
+
+        def put(a):
+            if a is None:
+                return None
+            t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+            if on_dev:
+                t = t.to("cuda", non_blocking=False)
+            else:
+                t = t.pin_memory()
+            self._keep.append(t)
+            return t.data_ptr()
+
+        self._p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
+        self._q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
+        flags = (0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
+        self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
+                                 prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
+                                 self._p.ctypes.data if self._p is not None else None,
+                                 self._q.ctypes.data if self._q is not None else None,
+                                 KFP_F64 if precision == "f64" else KFP_F32, flags)
+        nforce = int(prob.f_time.shape[0])
+        self.cdata = kfp_swr_problem(1 if on_dev else 0, put(prob.u0), nforce, put(prob.f_time),
+                                     put(prob.f_space), put(prob.bc_xin), put(prob.bc_v), put(prob.lam0))
+        if on_dev:
+            torch.cuda.current_stream().synchronize()
+        self.h = kfp_swr_create(self.desc, self.cdata, int(stream.cuda_stream))
+        self._keep.clear()  # inputs were copied
+
+    # -- iteration ---------------------------------------------------------------
+    def sweep(self, max_iters: int, tol: float = 0.0, tol_kind: int = 0, allow_notconv: bool = True) -> int:
+        return kfp_swr_sweep(self.h, max_iters, tol, tol_kind, allow_notconv=allow_notconv)
+
+    # -- results -----------------------------------------------------------------
+    def traces(self) -> np.ndarray:
+        p = self.prob
+        out = np.zeros((max(p.nstrips - 1, 0), 2, p.nt, p.nx + 1))
+        for j in range(p.nstrips - 1):
+            for side in range(2):
+                kfp_swr_traces(self.h, j, side, out[j, side].ctypes.data, 0)
+        return out
+
+    def set_traces(self, lam: np.ndarray) -> None:
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        kfp_swr_set_traces(self.h, lam.ctypes.data, 0)
+
+    def bands(self) -> np.ndarray:
+        p = self.prob
+        out = np.zeros((max(p.nstrips - 1, 0), 2, p.nt, p.overlap + 1, p.nx + 1))
+        for j in range(p.nstrips - 1):
+            for side in range(2):
+                kfp_swr_bands(self.h, j, side, out[j, side].ctypes.data, 0)
+        return out
+
+    def solution(self) -> np.ndarray:
+        out = np.zeros((self.prob.nv + 1, self.prob.nx + 1))
+        kfp_swr_solution(self.h, out.ctypes.data, 0)
+        return out
+
+    def solution_device(self):
+        out = self._torch.empty((self.prob.nv + 1, self.prob.nx + 1), dtype=self._torch.float64, device="cuda")
+        kfp_swr_solution(self.h, out.data_ptr(), 1)
+        return out
+
+    def error(self):
+        """(e_mis, e_chg, j_l2, history[iterations, 3])."""
+        st = kfp_swr_stats(self.h)
+        return kfp_swr_error(self.h, int(st["iterations"]))
+
+    def stats(self) -> dict:
+        return kfp_swr_stats(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            kfp_swr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP64 -- max-norm error <= 1e-12 relative to the oracle's max-norm for
+the solution, interface data and overlap values; the per-iteration norms e_mis and
+e_chg are differences of nearly equal numbers, so they are compared in absolute
+terms against 1e-12 times the scale of the values they are taken from.  FP32 --
+relative L2 error <= 1e-5 (the FP32 path rounds every step to 24 bits).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_4596_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+
+def _swr():
+    from paper_1306_4596_gb300 import swr
+    return swr
+
+
+def rel_max(a, b):
+    scale = max(np.abs(b).max(), 1e-300) if b.size else 1.0
+    return np.abs(a - b).max() / scale if a.size else 0.0
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0) if a.size else 0.0
+
+
+def run_gpu(prob, iters, precision="f64", **kw):
+    swr = _swr()
+    with swr.SWR(prob, precision, **kw) as s:
+        s.sweep(iters)
+        out = {"u_T": s.solution(), "lam": s.traces(), "bands": s.bands(), "hist": s.error()[3],
+               "stats": s.stats()}
+    return out
+
+
+def run_oracle(prob, iters):
+    lam = np.zeros(oracle.trace_shape(prob)) if prob.lam0 is None else prob.lam0.copy()
+    hist = []
+    bands = None
+    u_T = None
+    for _ in range(iters):
+        new, bands, u_T = oracle.swr_iteration(prob, lam)
+        hist.append(oracle.interface_norms(prob, bands, new, lam))
+        lam = new
+    return {"u_T": u_T, "lam": lam, "bands": bands, "hist": np.array(hist).reshape(iters, 3)}
+
+
+def check_f64(gpu, ref, prob):
+    assert rel_max(gpu["u_T"], ref["u_T"]) <= F64_TOL, rel_max(gpu["u_T"], ref["u_T"])
+    if prob.nstrips > 1:
+        assert rel_max(gpu["lam"], ref["lam"]) <= F64_TOL, rel_max(gpu["lam"], ref["lam"])
+        assert rel_max(gpu["bands"], ref["bands"]) <= F64_TOL, rel_max(gpu["bands"], ref["bands"])
+        uscale = max(np.abs(ref["bands"]).max(), 1e-300)
+        lscale = max(np.abs(ref["lam"]).max(), np.abs(prob.lam0).max() if prob.lam0 is not None else 0, 1e-300)
+        dh = np.abs(gpu["hist"] - ref["hist"])
+        assert dh[:, 0].max() <= F64_TOL * uscale, (dh[:, 0], uscale)
+        assert dh[:, 1].max() <= F64_TOL * lscale, (dh[:, 1], lscale)
+        nband = ref["bands"][:, 0].size
+        jtol = F64_TOL * uscale * math.sqrt(prob.dt * prob.hx * nband) * 4
+        assert np.abs(np.sqrt(gpu["hist"][:, 2]) - np.sqrt(ref["hist"][:, 2])).max() <= jtol
+
+
+def check_f32(gpu, ref, prob):
+    assert rel_l2(gpu["u_T"], ref["u_T"]) <= F32_TOL, rel_l2(gpu["u_T"], ref["u_T"])
+    if prob.nstrips > 1:
+        assert rel_l2(gpu["lam"], ref["lam"]) <= F32_TOL, rel_l2(gpu["lam"], ref["lam"])
+        assert rel_l2(gpu["bands"], ref["bands"]) <= F32_TOL, rel_l2(gpu["bands"], ref["bands"])
+
+
+SMALL_CASES = [
+    # (label, problem factory, iterations)
+    ("small_dirichlet", inputs.small_dirichlet, 6),
+    ("small_robin", inputs.small_robin, 6),
+    ("dirichlet_S3_ov2", lambda: inputs.random_data(37, 24, 7, 0.01, 3, 2, False, seed=1), 3),
+    ("robin_S4_ov0_pq", lambda: inputs.random_data(61, 32, 5, 0.01, 4, 0, True, p=3.0, q=1.5, seed=2), 3),
+    ("robin_S2_ov3_one_warp", lambda: inputs.random_data(29, 16, 4, 0.02, 2, 3, True, p=2.0, seed=3), 3),
+    ("robin_ragged_31_cols", lambda: inputs.random_data(30, 16, 4, 0.02, 2, 1, True, p=2.0, seed=4), 3),
+    ("two_columns", lambda: inputs.random_data(1, 8, 3, 0.2, 2, 1, False, seed=5), 3),
+    ("max_overlap", lambda: inputs.random_data(95, 60, 6, 0.005, 5, 11, True, p=5.0, seed=6), 3),
+    ("robin_max_overlap_odd", lambda: inputs.random_data(64, 30, 5, 0.005, 3, 9, True, p=5.0, q=2.0, seed=7), 3),
+    ("single_step", lambda: inputs.random_data(40, 16, 1, 0.01, 2, 2, True, seed=8), 2),
+    ("dirichlet_no_overlap", lambda: inputs.random_data(33, 16, 4, 0.01, 2, 0, False, seed=9), 3),
+    ("single_strip", lambda: inputs.random_data(70, 32, 5, 0.01, 1, 0, False, seed=10), 1),
+    ("bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=11), 2),
+    ("bumps_dirichlet_ov4", lambda: inputs.gaussian_bumps(130, 256, 30, 1.5e-3, 4, seed=12, overlap=4,
+                                                          robin=False), 2),
+]
+
+
+@pytest.mark.parametrize("label,factory,iters", SMALL_CASES, ids=[c[0] for c in SMALL_CASES])
+def test_f64_matches_oracle(label, factory, iters):
+    prob = factory()
+    ref = run_oracle(prob, iters) if prob.nstrips > 1 else {"u_T": oracle.monolithic(prob)}
+    gpu = run_gpu(prob, iters)
+    check_f64(gpu, ref, prob)
+
+
+@pytest.mark.parametrize("label,factory,iters", SMALL_CASES, ids=[c[0] for c in SMALL_CASES])
+def test_f32_matches_oracle(label, factory, iters):
+    prob = factory()
+    ref = run_oracle(prob, iters) if prob.nstrips > 1 else {"u_T": oracle.monolithic(prob)}
+    gpu = run_gpu(prob, iters, "f32")
+    check_f32(gpu, ref, prob)
+
+
+def test_f64_without_graph_is_bitwise_identical():
+    prob = inputs.random_data(61, 32, 5, 0.01, 4, 2, True, p=3.0, seed=13)
+    a = run_gpu(prob, 3)
+    b = run_gpu(prob, 3, graph=False)
+    for key in ("u_T", "lam", "bands", "hist"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_converged_gpu_equals_single_domain():
+    """Pin 3 on the GPU path: the converged iterate equals the single-domain solve."""
+    prob = inputs.manufactured(64, 64, 20, 0.1, nstrips=2, overlap=0, robin=True, p=8.0)
+    mono = oracle.monolithic(prob)
+    swr = _swr()
+    with swr.SWR(prob) as s:
+        n = s.sweep(300, 1e-14, 0)
+        u = s.solution()
+    assert n < 300
+    assert np.abs(u - mono).max() <= 1e-11
+
+
+def test_full_grid_of_the_at_scale_workload():
+    """The 2048 x 4096, 8-strip grid in the benchmark's launch configuration, on a
+    short window the oracle finishes in seconds (nt = 8)."""
+    prob = inputs.at_scale().replace(nt=8)
+    prob.f_time = prob.f_time[:, :9].copy()
+    ref = run_oracle(prob, 2)
+    check_f64(run_gpu(prob, 2), ref, prob)
+    check_f32(run_gpu(prob, 2, "f32"), ref, prob)
+
+
+def test_at_scale_properties():
+    """Full benchmark workload (2 iterations): deterministic, non-negative (maximum
+    principle with non-negative data), and resumable bit for bit from the exported
+    interface data."""
+    swr = _swr()
+    prob = inputs.at_scale()
+    with swr.SWR(prob) as s:
+        s.sweep(1)
+        lam1 = s.traces()
+        s.sweep(1)
+        u_a = s.solution()
+        hist_a = s.error()[3]
+    assert np.isfinite(u_a).all() and u_a.min() >= -1e-14
+    assert hist_a[1, 0] < hist_a[0, 0]
+    p2 = inputs.at_scale()
+    p2.lam0 = lam1
+    with swr.SWR(p2) as s:
+        s.sweep(1)
+        u_b = s.solution()
+        hist_b = s.error()[3]
+    assert np.array_equal(u_a, u_b)
+    assert np.array_equal(hist_a[1], hist_b[0])
+
+
+def test_resume_from_set_traces():
+    swr = _swr()
+    prob = inputs.random_data(45, 24, 6, 0.01, 3, 1, True, p=2.0, seed=14)
+    with swr.SWR(prob) as s:
+        s.sweep(4)
+        ref = s.traces()
+        hist = s.error()[3]
+    with swr.SWR(prob) as s:
+        s.sweep(2)
+        ck = s.traces()
+    with swr.SWR(prob) as s:
+        s.set_traces(ck)
+        s.sweep(2)
+        assert np.array_equal(s.traces(), ref)
+        assert np.array_equal(s.error()[3], hist[2:])
+
+
+def test_tolerance_stops_and_reports():
+    swr = _swr()
+    prob = inputs.small_dirichlet()
+    ref = oracle.swr_solve(prob, 50, 1e-10, 0)
+    with swr.SWR(prob) as s:
+        n = s.sweep(50, 1e-10, 0)
+        assert n == ref["iters"]
+        with pytest.raises(swr.KfpError) as ei:
+            swr.kfp_swr_sweep(s.h, 2, 1e-30, 1)
+        assert ei.value.status == swr.KFP_ENOTCONV
+
+
+def test_nan_input_is_reported():
+    swr = _swr()
+    prob = inputs.small_robin()
+    prob.u0 = prob.u0.copy()
+    prob.u0[10, 10] = np.nan
+    with swr.SWR(prob) as s:
+        with pytest.raises(swr.KfpError) as ei:
+            swr.kfp_swr_sweep(s.h, 2, 1e-8, 1)
+        assert ei.value.status == swr.KFP_ENUMERIC
+
+
+def test_host_inputs_match_device_inputs():
+    prob = inputs.random_data(50, 24, 5, 0.01, 3, 2, True, p=2.0, seed=15)
+    a = run_gpu(prob, 2, inputs_on="host")
+    b = run_gpu(prob, 2, inputs_on="device")
+    for key in ("u_T", "lam", "bands", "hist"):
+        assert np.array_equal(a[key], b[key]), key
