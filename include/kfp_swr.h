@@ -65,6 +65,7 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1 } kfp_precision;
 /* Flags of kfp_swr_desc.flags */
 #define KFP_FLAG_NO_GRAPH 1u  /* launch every kernel directly instead of replaying a CUDA graph */
 #define KFP_FLAG_PROFILE 2u   /* time the sweep, exchange and error kernels with CUDA events */
+#define KFP_FLAG_GENERIC 4u   /* use the plain sweep kernel even where the TMA-fed one applies */
 
 typedef struct {
   double x0, x1, v0, v1; /* box [x0,x1] x [v0,v1], x1 > x0, v1 > v0 */

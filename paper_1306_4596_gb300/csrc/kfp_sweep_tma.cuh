@@ -1,0 +1,360 @@
+// kfp_sweep_tma.cuh -- TMA-fed sweep pass (sm_103a).
+//
+// Same pass as sweep_pass_kernel (back-substitution of step k fused with the
+// elimination of step k+1 in the same row order, lanes = x-columns, warp-shuffle
+// upwind neighbour, halo lanes), but every per-row input is streamed into shared
+// memory by the tensor-memory accelerator ahead of use:
+//
+//   warp 4 (producer, one elected lane) issues, per chunk of kChunk rows,
+//     cp.async.bulk.tensor.2d loads of the block's [kChunk x kBoxW] tile of the
+//     elimination residue y^k (or u^0 in the first pass), the same tile of the
+//     forcing term, and the [kChunk x 24] tile of per-row coefficient records,
+//   into a ring of NST stages guarded by full/empty mbarriers;
+//   warps 0..3 (consumers) wait on the stage, run the row recurrences from shared
+//     memory and store y^{k+1} straight to global memory (coalesced).
+//
+// Coefficient record of one row, one column class and one pass direction (24 = 3
+// classes x 8 fields):
+//   0: -cp   back-substitution coefficient of step k (eliminated the other way)
+//   1: A  = g (1 - c_i)     2: B = g c_i        (upwind transport, c_i = |v_i| dt/hx)
+//   3: -g a (coupling to the previously eliminated row)
+//   4: g     5: g * 2dt/hv (Robin interface data)
+//   6: sign of v_i          7: row kind (0 interior, 1 x inflow, 2 v boundary,
+//                              3/4 Dirichlet top/bottom, 5/6 Robin top/bottom)
+// Identity rows (kinds 1-4) carry A = B = -g a = g = 0 (and G = 0), so that with zero
+// boundary data they need no branch; their data, the interface rows and rows whose
+// u^k is recorded are handled in the first and last chunk of a pass (general path).
+// An interior row costs four fused multiply-adds:
+//   u = y^k - cp u_prev;  y^{k+1} = A u + B u_nb - g a y_prev + G
+// with G = g dt a F pre-scaled once (FMODE 1, constant-in-time forcing), G = 0
+// (FMODE 0) or G = (g dt a(t^{k+1})) F (FMODE 2, one time-dependent term).
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel raises a flag that
+// the host reports as KFP_ETIMEOUT, and the producer drains the copies it issued.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kfp_kernels.cuh"
+
+namespace kfp {
+
+constexpr int kChunk = 16;                                   // rows per stage
+constexpr int kBoxW = kWarpsPerBlock * kOutCols + 4;         // 124 columns per tile
+constexpr int kRecW = 24;                                    // record row: 3 classes x 8
+constexpr int kRecPad = kChunk;                              // zero rows before/after each record table
+constexpr unsigned kSpinLimit = 1u << 26;                    // bounded mbarrier waits
+
+struct TmaMaps {
+  CUtensorMap state;   // Y0/Y1 stacked as [2 * rows][P] (buffer b at row offset b*rows)
+  CUtensorMap init;    // U0 [nv+1][P]
+  CUtensorMap force;   // FMODE 1: GF [2 * rows][P] (pass direction d at row offset d*rows);
+                       // FMODE 2: F [nv+1][P]
+  CUtensorMap rec;     // records [S * 2 * (Lmax + 2 kRecPad)][24]
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Integer stored bit-for-bit in a record slot (no floating-point conversion).
+__device__ __forceinline__ int slot_int(double v) { return (int)__double_as_longlong(v); }
+__device__ __forceinline__ int slot_int(float v) { return __float_as_int(v); }
+
+// Bounded wait: false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename T>
+struct TmaArgs {
+  PassArgs<T> p;       // geometry, strips, boundary data, traces, outputs
+  int rows;            // total strip rows (sum L_s)
+  int Lpad;            // Lmax + 2 kRecPad
+  int* flag;           // error flag (1 = a wait timed out)
+  int bc_data;         // caller gave x-inflow or v-boundary data (rows of kind 1/2 need it)
+};
+
+template <typename T, int NST>
+struct TmaSmem {
+  T tile[NST][kChunk][kBoxW];
+  T frc[NST][kChunk][kBoxW];
+  T rec[NST][kChunk][kRecW];
+  uint64_t full[NST];
+  uint64_t empty[NST];
+};
+
+// Record the outgoing interface data and the overlap values of u^k at row l.
+template <typename T, bool UP>
+__device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo& st, int s, int k, int l,
+                                           int m, bool out_lane, T u, T u_m1, T u_m2) {
+  const int ov = A.ov, nt = A.nt, nxp = A.nx + 1, lo = st.lo;
+  const bool robin_in = A.robin && ov >= 1;
+  if (st.has_top) {
+    const int aT = st.alpha_top - lo;
+    const int eT = robin_in ? (UP ? aT + 1 : aT - 1) : aT;
+    if (l >= aT && l <= aT + ov && out_lane)
+      A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)u;
+    if (l == eT && out_lane) {
+      double lam;
+      if (!A.robin) {
+        lam = (double)u;
+      } else if (ov >= 1) {
+        const double d = UP ? ((double)u - (double)u_m2) : ((double)u_m2 - (double)u);
+        lam = st.q_top * (double)u_m1 - d * A.inv_2hv;
+      } else {
+        lam = (st.p_top + st.q_top) * (double)u - A.lam_in[(((size_t)s * 2 + 0) * nt + (k - 1)) * nxp + m];
+      }
+      A.lam_next[(((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m] = lam;
+    }
+  }
+  if (st.has_bot) {
+    const int aB = st.alpha_bot - lo;
+    const int eB = robin_in ? (UP ? aB + ov + 1 : aB + ov - 1) : aB + ov;
+    if (l >= aB && l <= aB + ov && out_lane)
+      A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)u;
+    if (l == eB && out_lane) {
+      double lam;
+      if (!A.robin) {
+        lam = (double)u;
+      } else if (ov >= 1) {
+        const double d = UP ? ((double)u - (double)u_m2) : ((double)u_m2 - (double)u);
+        lam = st.p_bot * (double)u_m1 + d * A.inv_2hv;
+      } else {
+        lam = (st.p_bot + st.q_bot) * (double)u -
+              A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
+      }
+      A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
+    }
+  }
+}
+
+// Right-hand side override of a non-interior row (kinds 1..6), given the regular value.
+template <typename T>
+__device__ __forceinline__ T special_row(const PassArgs<T>& A, const StripInfo& st, int s, int kind, int k1, int i,
+                                      int m, bool in_dom, int inflow_side, T regular, T glam) {
+  const int nxp = A.nx + 1, nt = A.nt;
+  switch (kind) {
+    case 1:
+      return (A.bc_xin && inflow_side >= 0) ? (T)A.bc_xin[((size_t)k1 * 2 + inflow_side) * (A.nv + 1) + i] : T(0);
+    case 2:
+      return (A.bc_v && in_dom) ? (T)A.bc_v[((size_t)k1 * 2 + (i == 0 ? 0 : 1)) * nxp + m] : T(0);
+    case 3:
+      return in_dom ? (T)A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : T(0);
+    case 4:
+      return in_dom ? (T)A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : T(0);
+    case 5: {
+      const double lam = in_dom ? A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : 0.0;
+      return (T)((double)regular + (double)glam * lam);
+    }
+    case 6: {
+      const double lam = in_dom ? A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : 0.0;
+      return (T)((double)regular + (double)glam * lam);
+    }
+    default:
+      return regular;
+  }
+}
+
+// MODE 0: eliminate step 1 from u^0; 1: back-substitute step k, eliminate step k+1;
+// 2: back-substitute the last step and store u^nt.  FMODE: 0 no forcing, 1 folded
+// constant forcing, 2 one time-dependent term.
+template <typename T, bool UP, int MODE, int FMODE, int NST>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32)
+sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const int k) {
+  // The dynamic shared-memory base is at least 16-byte aligned, which is what an
+  // unswizzled TMA destination needs; using it directly (no integer round trip)
+  // keeps every tile access a shared-memory load.
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  const PassArgs<T>& A = X.p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.y;
+  const StripInfo st = A.strips[s];
+  const int L = st.L;
+  const int NC = (L + kChunk - 1) / kChunk;
+  constexpr bool kUseForce = (MODE != 2) && (FMODE != 0);
+  const int dir = UP ? 0 : 1;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&sm.full[q], 1);
+      mbar_init(&sm.empty[q], kWarpsPerBlock);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  auto chunk_l0 = [&](int c) { return UP ? c * kChunk : L - (c + 1) * kChunk; };
+
+  if (warp == kWarpsPerBlock) {
+    // ------------------------------ producer ------------------------------
+    if (lane == 0) {
+      const int x0 = blockIdx.x * (kWarpsPerBlock * kOutCols);
+      const unsigned bytes = (unsigned)(sizeof(T) * (kChunk * kBoxW * (kUseForce ? 2 : 1) + kChunk * kRecW));
+      const int cur = k & 1;
+      bool ok = true;
+      int issued = 0;
+      for (int c = 0; c < NC; ++c) {
+        const int q = c % NST, use = c / NST;
+        if (use > 0 && !mbar_wait(&sm.empty[q], (use - 1) & 1)) { ok = false; break; }
+        const int l0 = chunk_l0(c);
+        mbar_expect_tx(&sm.full[q], bytes);
+        if (MODE == 0) tma_load_2d(&sm.tile[q][0][0], &maps.init, x0, st.lo + l0, &sm.full[q]);
+        else tma_load_2d(&sm.tile[q][0][0], &maps.state, x0, cur * X.rows + st.rowoff + l0, &sm.full[q]);
+        if (kUseForce) {
+          if (FMODE == 1) tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, dir * X.rows + st.rowoff + l0, &sm.full[q]);
+          else tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, st.lo + l0, &sm.full[q]);
+        }
+        tma_load_2d(&sm.rec[q][0][0], &maps.rec, 0, (s * 2 + dir) * X.Lpad + kRecPad + l0, &sm.full[q]);
+        ++issued;
+      }
+      if (!ok) {
+        atomicExch(X.flag, 1);
+        // drain: wait (bounded) for every stage that still has copies in flight
+        for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c)
+          (void)mbar_wait(&sm.full[c % NST], (c / NST) & 1);
+      }
+    }
+    return;
+  }
+
+  // ------------------------------ consumers ------------------------------
+  const int wl = warp;
+  const int w = blockIdx.x * kWarpsPerBlock + wl;
+  const bool warp_live = w < A.W;
+  const int m = w * kOutCols - 1 + lane;
+  const int col = m + 1;
+  const bool in_dom = (m >= 0) && (m <= A.nx);
+  const bool out_lane = warp_live && in_dom && lane >= 1 && lane <= kOutCols;
+  const int cls = (m <= 0) ? 0 : (m >= A.nx ? 2 : 1);
+  const int inflow_side = (m == 0) ? 0 : (m == A.nx ? 1 : -1);
+  const int P = A.P;
+  T* __restrict__ Ynext = ((k + 1) & 1) ? A.Y1 : A.Y0;
+  const int k1 = k + 1;
+  T dtak = T(0);
+  if (FMODE == 2 && MODE != 2) dtak = (T)A.dta[(size_t)k1 * A.nforce];
+
+  // rows whose u^k is recorded (overlap and trace stencil), local indices: one window
+  // at the bottom interface and one at the top interface (empty windows: lo > hi)
+  int rloB = 1, rhiB = 0, rloT = 1, rhiT = 0;
+  if (MODE != 0) {
+    if (st.has_bot) { rloB = st.alpha_bot - st.lo - 1; rhiB = st.alpha_bot - st.lo + A.ov + 1; }
+    if (st.has_top) { rloT = st.alpha_top - st.lo - 1; rhiT = st.alpha_top - st.lo + A.ov + 1; }
+  }
+
+  T u_prev = T(0), u_m1 = T(0), u_m2 = T(0), y_prev = T(0);
+  const int step = UP ? P : -P;
+  for (int c = 0; c < NC; ++c) {
+    const int q = c % NST, use = c / NST;
+    if (!mbar_wait(&sm.full[q], use & 1)) {
+      atomicExch(X.flag, 1);
+      return;
+    }
+    const int l0 = chunk_l0(c);
+    const int l1 = l0 + kChunk - 1;
+    const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
+                                           (rloT <= rhiT && !(l1 < rloT || l0 > rhiT)));
+    // Strip-end rows (boundary / interface kinds), recorded rows, rows outside the strip
+    // and caller boundary data go through the general path; every other chunk is a
+    // run of 16 interior rows with no branch.
+    const bool general = X.bc_data || rec_chunk || c == 0 || c == NC - 1;
+    if (!general) {
+      const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
+      T* out = Ynext + (size_t)(st.rowoff + lf) * P + col;
+      T* outT = A.UT + (size_t)(st.rowoff + lf) * P + col;
+#pragma unroll
+      for (int t = 0; t < kChunk; ++t) {
+        const int r = UP ? t : (kChunk - 1 - t);
+        const T* rc = &sm.rec[q][r][cls * 8];
+        const T tile = sm.tile[q][r][wl * kOutCols + lane];
+        T u;
+        if (MODE == 0) {
+          u = tile;
+        } else {
+          u = fma(rc[0], u_prev, tile);
+          u_prev = u;
+          u_m2 = u_m1;
+          u_m1 = u;
+          if (MODE == 2) {
+            if (out_lane) *outT = u;
+            outT += step;
+            continue;
+          }
+        }
+        const T unb = shfl_val(u, lane - slot_int(rc[6]));
+        T gterm;
+        if (FMODE == 0) gterm = T(0);
+        else if (FMODE == 1) gterm = sm.frc[q][r][wl * kOutCols + lane];
+        else gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
+        const T xterm = fma(rc[1], u, fma(rc[2], unb, gterm));  // independent of y_prev
+        const T y = fma(rc[3], y_prev, xterm);
+        if (out_lane) *out = y;
+        out += step;
+        y_prev = y;
+      }
+    } else {
+#pragma unroll 1
+      for (int t = 0; t < kChunk; ++t) {
+        const int r = UP ? t : (kChunk - 1 - t);
+        const int l = l0 + r;
+        if (l < 0 || l >= L) continue;  // rows outside the strip (uniform)
+        const T* rc = &sm.rec[q][r][cls * 8];
+        T u;
+        if (MODE == 0) {
+          u = sm.tile[q][r][wl * kOutCols + lane];
+        } else {
+          u = fma(rc[0], u_prev, sm.tile[q][r][wl * kOutCols + lane]);
+          u_prev = u;
+          if (rec_chunk) record_row<T, UP>(A, st, s, k, l, m, out_lane, u, u_m1, u_m2);
+          u_m2 = u_m1;
+          u_m1 = u;
+          if (MODE == 2) {
+            if (out_lane) A.UT[(size_t)(st.rowoff + l) * P + col] = u;
+            continue;
+          }
+        }
+        const T unb = shfl_val(u, lane - slot_int(rc[6]));
+        T gterm = T(0);
+        if (FMODE == 1) gterm = sm.frc[q][r][wl * kOutCols + lane];
+        if (FMODE == 2) gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
+        T y = fma(rc[3], y_prev, fma(rc[1], u, fma(rc[2], unb, gterm)));
+        const int kind = slot_int(rc[7]);
+        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[5]);
+        if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
+        y_prev = y;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.empty[q]);
+  }
+}
+
+}  // namespace kfp

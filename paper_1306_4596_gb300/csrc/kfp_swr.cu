@@ -9,7 +9,9 @@
 // either as direct launches or as one replayed CUDA graph.
 #include "../../include/kfp_swr.h"
 #include "kfp_kernels.cuh"
+#include "kfp_sweep_tma.cuh"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -196,8 +198,14 @@ struct kfp_swr {
   std::string last_error;
 
   // device memory
+  void* Ybuf = nullptr;        // [2][rows][P]: Y0 = first half, Y1 = second half
   void* Y0 = nullptr;
   void* Y1 = nullptr;
+  void* GF = nullptr;          // [2][rows][P] pre-scaled forcing per pass direction (FMODE 1)
+  void* rec = nullptr;         // [S][2][Lpad][24] coefficient records
+  int* flag = nullptr;         // device error flag (bounded waits)
+  int use_tma = 0, fmode = 0, Lpad = 0;
+  kfp::TmaMaps maps;
   void* UT = nullptr;
   void* U0 = nullptr;
   void* F = nullptr;
@@ -272,6 +280,12 @@ struct kfp_swr {
 
   template <typename T>
   void enqueue_passes(cudaStream_t st) const {
+    if (use_tma) {
+      if (fmode == 0) enqueue_passes_tma<T, 0>(st);
+      else if (fmode == 1) enqueue_passes_tma<T, 1>(st);
+      else enqueue_passes_tma<T, 2>(st);
+      return;
+    }
     const kfp::PassArgs<T> A = pass_args<T>();
     const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
     const dim3 block(kfp::kWarpsPerBlock * 32);
@@ -283,6 +297,48 @@ struct kfp_swr {
     }
     if (g.nt & 1) kfp::sweep_pass_kernel<T, false, 2><<<grid, block, 0, st>>>(A, g.nt);
     else          kfp::sweep_pass_kernel<T, true, 2><<<grid, block, 0, st>>>(A, g.nt);
+  }
+
+  template <typename T>
+  static constexpr int tma_stages() { return sizeof(T) == 8 ? 4 : 8; }
+  template <typename T>
+  static size_t tma_smem_bytes() { return sizeof(kfp::TmaSmem<T, tma_stages<T>()>) + 128; }
+
+  template <typename T, int FM>
+  void enqueue_passes_tma(cudaStream_t st) const {
+    constexpr int NST = tma_stages<T>();
+    kfp::TmaArgs<T> X;
+    X.p = pass_args<T>();
+    X.rows = g.rows;
+    X.Lpad = Lpad;
+    X.flag = flag;
+    X.bc_data = (bc_xin || bc_v) ? 1 : 0;
+    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
+    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
+    const size_t sm = tma_smem_bytes<T>();
+    kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<grid, block, sm, st>>>(maps, X, 0);
+    for (int k = 1; k < g.nt; ++k) {
+      if (k & 1) kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+      else       kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+    }
+    if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
+    else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
+  }
+
+  template <typename T, int FM>
+  cudaError_t set_tma_smem_attr() const {
+    constexpr int NST = tma_stages<T>();
+    const int sm = (int)tma_smem_bytes<T>();
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* fn) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    };
+    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST>);
+    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST>);
+    set((const void*)kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST>);
+    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST>);
+    set((const void*)kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST>);
+    return e;
   }
 
   void record(int idx, cudaStream_t st, bool capturing) const {
@@ -405,6 +461,11 @@ struct kfp_swr {
     iterations += done;
     if (iters_done) *iters_done = done;
     if (rc) return rc;
+    if (use_tma) {
+      int f = 0;
+      KFP_CUDA_TRY(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
+      if (f) return fail(KFP_ETIMEOUT, "a bounded wait in the sweep kernel expired");
+    }
     if (g.S > 1) {
       const double* last = &history[history.size() - 3];
       if (!std::isfinite(last[0]) || !std::isfinite(last[1]) || !std::isfinite(last[2]))
@@ -420,7 +481,7 @@ struct kfp_swr {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    void* bufs[] = {Y0, Y1, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
+    void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage};
     for (void* b : bufs)
       if (b) cudaFree(b);
@@ -469,6 +530,170 @@ kfp_status copy_in(kfp_swr* h, void* dst, const void* src, size_t bytes, int on_
   return KFP_OK;
 }
 
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2D row-major tensor [rows][cols] of T, tile box [box_rows][box_cols].
+kfp_status encode_2d(kfp_swr* h, CUtensorMap* map, void* base, size_t rows, size_t cols, int box_rows,
+                     int box_cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return h->fail(KFP_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const size_t es = h->elem();
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)(cols * es)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim,
+                  gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return h->fail(KFP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return KFP_OK;
+}
+
+template <typename T>
+void put_bits(T* slot, long long v) {
+  if (sizeof(T) == 8) std::memcpy(slot, &v, 8);
+  else { int x = (int)v; std::memcpy(slot, &x, 4); }
+}
+
+// Coefficient records [S][2 pass directions][Lpad][3 classes][8] (see kfp_sweep_tma.cuh)
+// and, for one constant-in-time forcing term, G = g dt a F per pass direction.
+template <typename T>
+kfp_status build_records(kfp_swr* h, const std::vector<double>& coef, const std::vector<double>& Fh, double a0,
+                         std::vector<T>* rec_out, std::vector<T>* gf_out) {
+  const Geometry& g = h->g;
+  const int Lpad = h->Lpad, Lm = g.Lmax;
+  rec_out->assign((size_t)g.S * 2 * Lpad * kfp::kRecW, T(0));
+  const double two_dt_hv = 2.0 * g.dt / g.hv;
+  for (int s = 0; s < g.S; ++s) {
+    const kfp::StripInfo& st = g.strips[s];
+    for (int dir = 0; dir < 2; ++dir) {          // pass direction: 0 ascending, 1 descending
+      const int dE = dir, dB = 1 - dir;           // elimination of step k+1 / of step k
+      for (int cls = 0; cls < 3; ++cls) {
+        const double* cE = &coef[(((size_t)s * 3 + cls) * 2 + dE) * 3 * Lm];
+        const double* cB = &coef[(((size_t)s * 3 + cls) * 2 + dB) * 3 * Lm];
+        for (int l = 0; l < st.L; ++l) {
+          const int i = st.lo + l;
+          const double vi = g.v0 + i * g.hv;
+          const double cab = std::fabs(vi * g.dt / g.hx);
+          const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
+          int kind = 0;
+          if (i == 0 || i == g.nv) kind = 2;
+          else if (inflow) kind = 1;
+          else if (st.has_top && i == st.hi) kind = g.robin ? 5 : 3;
+          else if (st.has_bot && i == st.lo) kind = g.robin ? 6 : 4;
+          const double gE = cE[0 * Lm + l], aE = cE[1 * Lm + l], cpB = cB[2 * Lm + l];
+          T* r = &(*rec_out)[(((size_t)s * 2 + dir) * Lpad + kfp::kRecPad + l) * kfp::kRecW + cls * 8];
+          const bool ident = kind >= 1 && kind <= 4;
+          r[0] = (T)(-cpB);
+          r[1] = ident ? T(0) : (T)(gE * (1.0 - cab));
+          r[2] = ident ? T(0) : (T)(gE * cab);
+          r[3] = ident ? T(0) : (T)(-gE * aE);
+          r[4] = ident ? T(0) : (T)gE;
+          r[5] = (T)(gE * two_dt_hv);
+          put_bits(&r[6], vi > 0 ? 1 : (vi < 0 ? -1 : 0));
+          put_bits(&r[7], kind);
+        }
+      }
+    }
+  }
+  if (gf_out) {
+    gf_out->assign((size_t)2 * g.rows * g.P, T(0));
+    const size_t nxp = g.nx + 1;
+    for (int dir = 0; dir < 2; ++dir)
+      for (int s = 0; s < g.S; ++s) {
+        const kfp::StripInfo& st = g.strips[s];
+        for (int l = 0; l < st.L; ++l) {
+          const int i = st.lo + l;
+          T* row = &(*gf_out)[((size_t)dir * g.rows + st.rowoff + l) * g.P];
+          const double vi = g.v0 + i * g.hv;
+          const bool vbnd = (i == 0 || i == g.nv);
+          const bool dir_if = !g.robin && ((st.has_top && i == st.hi) || (st.has_bot && i == st.lo));
+          for (int m = 0; m <= g.nx; ++m) {
+            const int cls = m == 0 ? 0 : (m == g.nx ? 2 : 1);
+            const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
+            const double gE = coef[(((size_t)s * 3 + cls) * 2 + dir) * 3 * Lm + l];
+            row[m + 1] = (vbnd || inflow || dir_if) ? T(0) : (T)(gE * (g.dt * a0) * Fh[(size_t)i * nxp + m]);
+          }
+        }
+      }
+  }
+  return KFP_OK;
+}
+
+template <typename T>
+kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
+  Geometry& g = h->g;
+  const size_t nxp = g.nx + 1;
+  // forcing mode: none, one constant-in-time term (pre-scaled), one time-dependent term
+  double a0 = 0.0;
+  std::vector<double> Fh;
+  if (g.nforce == 0) {
+    h->fmode = 0;
+  } else {
+    std::vector<double> ft(g.nt + 1);
+    KFP_CUDA_TRY_H(cudaMemcpy(ft.data(), pb->f_time, sizeof(double) * ft.size(),
+                              pb->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    bool constant = true;
+    for (int n = 2; n <= g.nt; ++n) constant = constant && (ft[n] == ft[1]);
+    h->fmode = constant ? 1 : 2;
+    a0 = ft[1];
+    if (h->fmode == 1) {
+      Fh.resize((size_t)(g.nv + 1) * nxp);
+      KFP_CUDA_TRY_H(cudaMemcpy(Fh.data(), pb->f_space, sizeof(double) * Fh.size(),
+                                pb->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    }
+  }
+  h->Lpad = g.Lmax + 2 * kfp::kRecPad;
+  std::vector<double> coef = build_factors(g);
+  std::vector<T> rec, gf;
+  kfp_status rc = build_records<T>(h, coef, Fh, a0, &rec, h->fmode == 1 ? &gf : nullptr);
+  if (rc) return rc;
+  rc = alloc(h, &h->rec, sizeof(T) * rec.size());
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemcpy(h->rec, rec.data(), sizeof(T) * rec.size(), cudaMemcpyHostToDevice));
+  if (h->fmode == 1) {
+    rc = alloc(h, &h->GF, sizeof(T) * gf.size());
+    if (rc) return rc;
+    KFP_CUDA_TRY_H(cudaMemcpy(h->GF, gf.data(), sizeof(T) * gf.size(), cudaMemcpyHostToDevice));
+  }
+  rc = alloc(h, (void**)&h->flag, sizeof(int));
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemset(h->flag, 0, sizeof(int)));
+  // tensor maps
+  rc = encode_2d(h, &h->maps.state, h->Ybuf, (size_t)2 * g.rows, g.P, kfp::kChunk, kfp::kBoxW);
+  if (!rc) rc = encode_2d(h, &h->maps.init, h->U0, g.nv + 1, g.P, kfp::kChunk, kfp::kBoxW);
+  if (!rc && h->fmode == 1) rc = encode_2d(h, &h->maps.force, h->GF, (size_t)2 * g.rows, g.P, kfp::kChunk, kfp::kBoxW);
+  if (!rc && h->fmode == 2) rc = encode_2d(h, &h->maps.force, h->F, g.nv + 1, g.P, kfp::kChunk, kfp::kBoxW);
+  if (!rc && h->fmode == 0) h->maps.force = h->maps.init;  // never read
+  if (!rc) rc = encode_2d(h, &h->maps.rec, h->rec, (size_t)g.S * 2 * h->Lpad, kfp::kRecW, kfp::kChunk, kfp::kRecW);
+  if (rc) return rc;
+  cudaError_t e = h->fmode == 0 ? h->set_tma_smem_attr<T, 0>()
+                                : (h->fmode == 1 ? h->set_tma_smem_attr<T, 1>() : h->set_tma_smem_attr<T, 2>());
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
+  h->use_tma = 1;
+  return KFP_OK;
+}
+
+kfp_status setup_tma(kfp_swr* h, const kfp_swr_problem* pb) {
+  return h->prec == KFP_F64 ? setup_tma_t<double>(h, pb) : setup_tma_t<float>(h, pb);
+}
+
 kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem* pb) {
   Geometry& g = h->g;
   const size_t es = h->elem();
@@ -481,13 +706,13 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   } while (0)
   // state buffers
   const size_t ystate = (size_t)g.rows * g.P * es;
-  TRY(alloc(h, &h->Y0, ystate));
-  TRY(alloc(h, &h->Y1, ystate));
+  TRY(alloc(h, &h->Ybuf, 2 * ystate));
+  h->Y0 = h->Ybuf;
+  h->Y1 = (char*)h->Ybuf + ystate;
   TRY(alloc(h, &h->UT, ystate));
   TRY(alloc(h, &h->U0, (size_t)(g.nv + 1) * g.P * es));
   TRY(alloc(h, &h->F, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es));
-  cudaMemsetAsync(h->Y0, 0, ystate, h->stream);
-  cudaMemsetAsync(h->Y1, 0, ystate, h->stream);
+  cudaMemsetAsync(h->Ybuf, 0, 2 * ystate, h->stream);
   cudaMemsetAsync(h->UT, 0, ystate, h->stream);
   cudaMemsetAsync(h->U0, 0, (size_t)(g.nv + 1) * g.P * es, h->stream);
   cudaMemsetAsync(h->F, 0, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es, h->stream);
@@ -541,6 +766,12 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
     KFP_CUDA_TRY_H(cudaMemcpy(h->strips, g.strips.data(), sizeof(kfp::StripInfo) * g.S, cudaMemcpyHostToDevice));
     TRY(alloc(h, (void**)&h->row_of, sizeof(int) * (g.nv + 1)));
     KFP_CUDA_TRY_H(cudaMemcpy(h->row_of, g.row_of.data(), sizeof(int) * (g.nv + 1), cudaMemcpyHostToDevice));
+  }
+
+  // TMA-fed sweep: records, pre-scaled forcing, tensor maps
+  if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
+    rc = setup_tma(h, pb);
+    if (rc) return rc;
   }
 
   // boundary data

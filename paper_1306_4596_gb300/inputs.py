@@ -164,17 +164,25 @@ def error_equation(nx: int, nv: int, nt: int, dt: float, nstrips: int, overlap: 
 
 
 def random_data(nx: int, nv: int, nt: int, dt: float, nstrips: int, overlap: int, robin: bool,
-                p=2.0, q=None, seed: int = 0, nforce: int = 2, v_range=(-1.0, 1.0)) -> Problem:
+                p=2.0, q=None, seed: int = 0, nforce: int = 2, v_range=(-1.0, 1.0),
+                constant_in_time: bool = False, boundary_data: bool = True) -> Problem:
     """Every input drawn at random (rng = default_rng(seed), draw order: u0, f_time,
     f_space, bc_xin, bc_v, lam0; all U[-1, 1]).  Exercises every data path: both
-    inflow sides, both v boundaries, several forcing terms and nonzero traces."""
+    inflow sides, both v boundaries, forcing terms and nonzero traces.  With
+    ``constant_in_time`` every a_r(t^n) equals its value at n = 1; without
+    ``boundary_data`` the inflow and v-boundary data are zero (passed as None),
+    after the same draws."""
     rng = np.random.default_rng(seed)
     u0 = rng.uniform(-1, 1, (nv + 1, nx + 1))
     f_time = rng.uniform(-1, 1, (nforce, nt + 1))
+    if constant_in_time:
+        f_time[:, 1:] = f_time[:, 1:2]
     f_space = rng.uniform(-1, 1, (nforce, nv + 1, nx + 1))
     bc_xin = rng.uniform(-1, 1, (nt + 1, 2, nv + 1))
     bc_v = rng.uniform(-1, 1, (nt + 1, 2, nx + 1))
     lam0 = rng.uniform(-1, 1, (max(nstrips - 1, 0), 2, nt, nx + 1))
+    if not boundary_data:
+        bc_xin = bc_v = None
     pp, qq = _pq(nstrips, p, q)
     return Problem(0.0, 1.0, v_range[0], v_range[1], dt, nx, nv, nt, nstrips, overlap, robin, pp, qq,
                    u0, f_time, f_space, bc_xin, bc_v, lam0,

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "KFP_OK", 1: "KFP_EINVAL", 2: "KFP_ECFL", 3: "KFP_ENOMEM", 4:
                 5: "KFP_ENOTCONV", 6: "KFP_ENUMERIC", 7: "KFP_ETIMEOUT", 8: "KFP_ENOTSUP"}
 KFP_DIRICHLET, KFP_ROBIN = 0, 1
 KFP_F64, KFP_F32 = 0, 1
-KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE = 1, 2
+KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC = 1, 2, 4
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
@@ -181,7 +181,7 @@ class SWR:
     handed over and the library copies them in."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
-                 graph: bool = True, profile: bool = False):
+                 graph: bool = True, profile: bool = False, generic: bool = False):
         import torch
 
         self.prob = prob
@@ -206,7 +206,8 @@ class SWR:
 
         self._p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
         self._q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
-        flags = (0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
+        flags = ((0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
+                 | (KFP_FLAG_GENERIC if generic else 0))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
                                  self._p.ctypes.data if self._p is not None else None,

@@ -78,20 +78,36 @@ def check_f32(gpu, ref, prob):
         assert rel_l2(gpu["bands"], ref["bands"]) <= F32_TOL, rel_l2(gpu["bands"], ref["bands"])
 
 
+RD = inputs.random_data
 SMALL_CASES = [
-    # (label, problem factory, iterations)
+    # (label, problem factory, iterations).  One forcing term (time-dependent or
+    # constant) and no forcing run the TMA-fed sweep; two terms run the plain one.
     ("small_dirichlet", inputs.small_dirichlet, 6),
     ("small_robin", inputs.small_robin, 6),
-    ("dirichlet_S3_ov2", lambda: inputs.random_data(37, 24, 7, 0.01, 3, 2, False, seed=1), 3),
-    ("robin_S4_ov0_pq", lambda: inputs.random_data(61, 32, 5, 0.01, 4, 0, True, p=3.0, q=1.5, seed=2), 3),
-    ("robin_S2_ov3_one_warp", lambda: inputs.random_data(29, 16, 4, 0.02, 2, 3, True, p=2.0, seed=3), 3),
-    ("robin_ragged_31_cols", lambda: inputs.random_data(30, 16, 4, 0.02, 2, 1, True, p=2.0, seed=4), 3),
-    ("two_columns", lambda: inputs.random_data(1, 8, 3, 0.2, 2, 1, False, seed=5), 3),
-    ("max_overlap", lambda: inputs.random_data(95, 60, 6, 0.005, 5, 11, True, p=5.0, seed=6), 3),
-    ("robin_max_overlap_odd", lambda: inputs.random_data(64, 30, 5, 0.005, 3, 9, True, p=5.0, q=2.0, seed=7), 3),
-    ("single_step", lambda: inputs.random_data(40, 16, 1, 0.01, 2, 2, True, seed=8), 2),
-    ("dirichlet_no_overlap", lambda: inputs.random_data(33, 16, 4, 0.01, 2, 0, False, seed=9), 3),
-    ("single_strip", lambda: inputs.random_data(70, 32, 5, 0.01, 1, 0, False, seed=10), 1),
+    ("dirichlet_S3_ov2", lambda: RD(37, 24, 7, 0.01, 3, 2, False, seed=1, nforce=1), 3),
+    ("robin_S4_ov0_pq", lambda: RD(61, 32, 5, 0.01, 4, 0, True, p=3.0, q=1.5, seed=2, nforce=1), 3),
+    ("robin_S2_ov3_one_warp", lambda: RD(29, 16, 4, 0.02, 2, 3, True, p=2.0, seed=3, nforce=1), 3),
+    ("robin_ragged_31_cols", lambda: RD(30, 16, 4, 0.02, 2, 1, True, p=2.0, seed=4, nforce=1), 3),
+    ("two_columns", lambda: RD(1, 8, 3, 0.2, 2, 1, False, seed=5, nforce=1), 3),
+    ("max_overlap", lambda: RD(95, 60, 6, 0.005, 5, 11, True, p=5.0, seed=6, nforce=1), 3),
+    ("robin_max_overlap_odd", lambda: RD(64, 30, 5, 0.005, 3, 9, True, p=5.0, q=2.0, seed=7, nforce=1), 3),
+    ("single_step", lambda: RD(40, 16, 1, 0.01, 2, 2, True, seed=8, nforce=1), 2),
+    ("dirichlet_no_overlap", lambda: RD(33, 16, 4, 0.01, 2, 0, False, seed=9, nforce=1), 3),
+    ("single_strip", lambda: RD(70, 32, 5, 0.01, 1, 0, False, seed=10, nforce=1), 1),
+    ("no_forcing", lambda: RD(150, 40, 7, 0.005, 4, 2, True, p=3.0, seed=16, nforce=0), 3),
+    ("constant_forcing", lambda: RD(200, 64, 9, 0.004, 4, 0, True, p=3.0, seed=17, nforce=1,
+                                    constant_in_time=True), 3),
+    ("two_forcing_terms", lambda: RD(61, 32, 5, 0.01, 4, 1, True, p=3.0, seed=18, nforce=2), 3),
+    ("long_strips_many_chunks", lambda: RD(250, 400, 6, 2e-4, 2, 3, True, p=6.0, seed=19, nforce=1,
+                                           v_range=(-2.0, 2.0)), 2),
+    # zero boundary data and long strips: interior chunks take the branch-free path
+    ("fast_dirichlet_ov3", lambda: RD(90, 256, 6, 0.002, 2, 3, False, seed=20, nforce=1, boundary_data=False), 3),
+    ("fast_robin_pq_time_forcing", lambda: RD(77, 192, 5, 0.002, 3, 0, True, p=4.0, q=2.0, seed=21, nforce=1,
+                                              boundary_data=False), 3),
+    ("fast_no_forcing_ov5", lambda: RD(64, 128, 5, 0.003, 2, 5, True, p=3.0, seed=22, nforce=0,
+                                       boundary_data=False), 3),
+    ("fast_const_forcing_S3", lambda: RD(120, 300, 4, 0.002, 3, 4, True, p=5.0, seed=23, nforce=1,
+                                         constant_in_time=True, boundary_data=False), 3),
     ("bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=11), 2),
     ("bumps_dirichlet_ov4", lambda: inputs.gaussian_bumps(130, 256, 30, 1.5e-3, 4, seed=12, overlap=4,
                                                           robin=False), 2),
@@ -112,6 +128,15 @@ def test_f32_matches_oracle(label, factory, iters):
     ref = run_oracle(prob, iters) if prob.nstrips > 1 else {"u_T": oracle.monolithic(prob)}
     gpu = run_gpu(prob, iters, "f32")
     check_f32(gpu, ref, prob)
+
+
+@pytest.mark.parametrize("label,factory,iters", SMALL_CASES[:6] + SMALL_CASES[12:14],
+                         ids=[c[0] for c in SMALL_CASES[:6] + SMALL_CASES[12:14]])
+def test_f64_plain_kernel_matches_oracle(label, factory, iters):
+    """The plain (non-TMA) sweep kernel on the cases the TMA-fed one normally takes."""
+    prob = factory()
+    ref = run_oracle(prob, iters) if prob.nstrips > 1 else {"u_T": oracle.monolithic(prob)}
+    check_f64(run_gpu(prob, iters, generic=True), ref, prob)
 
 
 def test_f64_without_graph_is_bitwise_identical():
