@@ -16,16 +16,17 @@
 // Coefficient record of one row, one column class and one pass direction (24 = 3
 // classes x 8 fields):
 //   0: -cp   back-substitution coefficient of step k (eliminated the other way)
-//   1: A  = g (1 - c_i)     2: B = g c_i        (upwind transport, c_i = |v_i| dt/hx)
-//   3: -g a (coupling to the previously eliminated row)
-//   4: g     5: g * 2dt/hv (Robin interface data)
-//   6: sign of v_i          7: row kind (0 interior, 1 x inflow, 2 v boundary,
-//                              3/4 Dirichlet top/bottom, 5/6 Robin top/bottom)
+//   1: sign of v_i (integer bits)
+//   2: A  = g (1 - c_i)     3: B = g c_i        (upwind transport, c_i = |v_i| dt/hx)
+//   4: -g a (coupling to the previously eliminated row)
+//   5: g     6: g * 2dt/hv (Robin interface data)
+//   7: row kind (integer bits: 0 interior, 1 x inflow, 2 v boundary,
+//      3/4 Dirichlet top/bottom, 5/6 Robin top/bottom)
 // Identity rows (kinds 1-4) carry A = B = -g a = g = 0 (and G = 0), so that with zero
 // boundary data they need no branch; their data, the interface rows and rows whose
 // u^k is recorded are handled in the first and last chunk of a pass (general path).
 // An interior row costs four fused multiply-adds:
-//   u = y^k - cp u_prev;  y^{k+1} = A u + B u_nb - g a y_prev + G
+//   u = y^k - cp u_prev;  y^{k+1} = (A u + B u_nb + G) - g a y_prev
 // with G = g dt a F pre-scaled once (FMODE 1, constant-in-time forcing), G = 0
 // (FMODE 0) or G = (g dt a(t^{k+1})) F (FMODE 2, one time-dependent term).
 //
@@ -287,38 +288,56 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     // run of 16 interior rows with no branch.
     const bool general = X.bc_data || rec_chunk || c == 0 || c == NC - 1;
     if (!general) {
+      // Phased chunk: (1) the back-substitution chain u for 16 rows, (2) shuffles and
+      // the terms that do not depend on the previous row, (3) the elimination chain
+      // y.  Each phase is a run of independent or singly chained FMAs, so in-order
+      // issue never waits on a shuffle inside a chain.
       const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
-      T* out = Ynext + (size_t)(st.rowoff + lf) * P + col;
-      T* outT = A.UT + (size_t)(st.rowoff + lf) * P + col;
+      const int cbase = wl * kOutCols + lane;
+      T uu[kChunk];
 #pragma unroll
       for (int t = 0; t < kChunk; ++t) {
         const int r = UP ? t : (kChunk - 1 - t);
-        const T* rc = &sm.rec[q][r][cls * 8];
-        const T tile = sm.tile[q][r][wl * kOutCols + lane];
-        T u;
+        const T tile = sm.tile[q][r][cbase];
         if (MODE == 0) {
-          u = tile;
+          uu[t] = tile;
         } else {
-          u = fma(rc[0], u_prev, tile);
-          u_prev = u;
-          u_m2 = u_m1;
-          u_m1 = u;
-          if (MODE == 2) {
-            if (out_lane) *outT = u;
-            outT += step;
-            continue;
-          }
+          u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile);
+          uu[t] = u_prev;
         }
-        const T unb = shfl_val(u, lane - slot_int(rc[6]));
-        T gterm;
-        if (FMODE == 0) gterm = T(0);
-        else if (FMODE == 1) gterm = sm.frc[q][r][wl * kOutCols + lane];
-        else gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
-        const T xterm = fma(rc[1], u, fma(rc[2], unb, gterm));  // independent of y_prev
-        const T y = fma(rc[3], y_prev, xterm);
-        if (out_lane) *out = y;
-        out += step;
-        y_prev = y;
+      }
+      if (MODE != 0) {
+        u_m2 = uu[kChunk - 2];
+        u_m1 = uu[kChunk - 1];
+      }
+      if (MODE == 2) {
+        T* outT = A.UT + (size_t)(st.rowoff + lf) * P + col;
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) {
+          if (out_lane) *outT = uu[t];
+          outT += step;
+        }
+      } else {
+        T xx[kChunk];
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) {
+          const int r = UP ? t : (kChunk - 1 - t);
+          const T* rc = &sm.rec[q][r][cls * 8];
+          const T unb = shfl_val(uu[t], lane - slot_int(rc[1]));
+          T gterm;
+          if (FMODE == 0) gterm = T(0);
+          else if (FMODE == 1) gterm = sm.frc[q][r][cbase];
+          else gterm = (rc[5] * dtak) * sm.frc[q][r][cbase];
+          xx[t] = fma(rc[2], uu[t], fma(rc[3], unb, gterm));
+        }
+        T* out = Ynext + (size_t)(st.rowoff + lf) * P + col;
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) {
+          const int r = UP ? t : (kChunk - 1 - t);
+          y_prev = fma(sm.rec[q][r][cls * 8 + 4], y_prev, xx[t]);
+          if (out_lane) *out = y_prev;
+          out += step;
+        }
       }
     } else {
 #pragma unroll 1
@@ -341,13 +360,13 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
             continue;
           }
         }
-        const T unb = shfl_val(u, lane - slot_int(rc[6]));
+        const T unb = shfl_val(u, lane - slot_int(rc[1]));
         T gterm = T(0);
         if (FMODE == 1) gterm = sm.frc[q][r][wl * kOutCols + lane];
-        if (FMODE == 2) gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
-        T y = fma(rc[3], y_prev, fma(rc[1], u, fma(rc[2], unb, gterm)));
+        if (FMODE == 2) gterm = (rc[5] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
+        T y = fma(rc[4], y_prev, fma(rc[2], u, fma(rc[3], unb, gterm)));
         const int kind = slot_int(rc[7]);
-        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[5]);
+        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[6]);
         if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
         y_prev = y;
       }
