@@ -155,6 +155,39 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
                          int* launches_per_iter, double* sweep_ms, double* exchange_ms,
                          double* error_ms);
 
+/* Largest interface count accepted by kfp_iface_norms_noalloc. */
+#define KFP_NOALLOC_MAX_INTERFACES 64
+
+/*
+ * Interface norms computed without allocating memory.  The paper has no
+ * counterpart: this entry point serves callers that may not allocate device memory
+ * themselves or let a library do so -- for example code running inside a host
+ * application that owns every device allocation and hands a plugin only its input
+ * and output buffers, or a latency-critical loop that cannot afford cudaMalloc
+ * (which can synchronise the device and takes the allocator's lock).
+ *
+ * bands: device memory, [nif][2][nt][overlap_cells+1][nx+1] FP64, the layout of
+ *   kfp_swr_bands ([j][0] = lower strip, [j][1] = upper strip of interface j).
+ * out:   device memory, 2 + 2*nif doubles, written by the kernel:
+ *   out[0] = e_mis = max |lower - upper|, out[1] = j_l2 = dt hx sum (lower - upper)^2,
+ *   out[2+2j], out[3+2j] = the same two norms of interface j alone.
+ * The work is enqueued on cuda_stream (NULL = legacy default stream); nothing is
+ * synchronised except during the set-up below.
+ *
+ * Scratch: a file-scope device array of 64 x 32 x 2 doubles plus a counter
+ * (32 KiB) that every GPU which loads this library keeps until the process exits.
+ * The first call on a device does a one-time set-up with that device current (it
+ * looks up the array's device address and zeroes the counter, then synchronises
+ * the device), so make that first call before any stream capture.  Every call
+ * shares the array: calls whose kernels can overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: KFP_EINVAL for NULL pointers, non-positive sizes or nif >
+ * KFP_NOALLOC_MAX_INTERFACES; KFP_ECUDA if the set-up or the launch fails.
+ * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ */
+kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx, double dt,
+                                   double hx, double* out, void* cuda_stream);
+
 /* Free every resource of the handle (NULL is ignored).  Synchronises its stream. */
 void kfp_swr_destroy(kfp_swr_t h);
 

@@ -1,6 +1,7 @@
 """Build the sm_103a shared library ``_build/libkfp_swr.so`` with nvcc.
 
-One translation unit (``csrc/kfp_swr.cu``, which includes the kernels), one
+Two translation units (``csrc/kfp_swr.cu``, which includes the kernels, and
+``csrc/kfp_noalloc.cu``), one
 ``-gencode`` (compute_103a / sm_103a), built in-tree so that the process loading
 it is seen using it.  Host code is compiled without floating-point contraction so
 that its setup arithmetic (grid nodes, factors) rounds the same on x86 and Arm.
@@ -16,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkfp_swr.so")
-SOURCES = [os.path.join(CSRC, "kfp_swr.cu")]
+SOURCES = [os.path.join(CSRC, "kfp_swr.cu"), os.path.join(CSRC, "kfp_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, "kfp_swr.h")]
 

@@ -26,7 +26,8 @@ KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC = 1, 2, 4
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
-            "kfp_swr_last_error", "kfp_swr_create_error")
+            "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc")
+KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -80,6 +81,8 @@ def load(rebuild: bool = False):
             lib.kfp_swr_destroy.restype = None
             lib.kfp_swr_last_error.argtypes = [vp]
             lib.kfp_swr_last_error.restype = ctypes.c_char_p
+            lib.kfp_iface_norms_noalloc.argtypes = [vp, i, i, i, i, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.kfp_iface_norms_noalloc.restype = ctypes.c_int
             lib.kfp_swr_create_error.argtypes = []
             lib.kfp_swr_create_error.restype = ctypes.c_char_p
             for name in ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces",
@@ -152,6 +155,20 @@ def kfp_swr_stats(h: int) -> dict:
 def kfp_swr_destroy(h: int) -> None:
     if h:
         load().kfp_swr_destroy(h)
+
+
+def kfp_iface_norms_noalloc(bands_ptr: int, nif: int, nt: int, overlap_cells: int, nx: int, dt: float, hx: float,
+                            out_ptr: int, cuda_stream: int = 0) -> None:
+    """Interface norms from device-resident overlap values, with no allocation (see the header)."""
+    st = load().kfp_iface_norms_noalloc(bands_ptr, nif, nt, overlap_cells, nx, dt, hx, out_ptr, cuda_stream)
+    if st != KFP_OK:
+        if st == KFP_EINVAL and nif > KFP_NOALLOC_MAX_INTERFACES:
+            msg = f"nif = {nif} exceeds KFP_NOALLOC_MAX_INTERFACES = {KFP_NOALLOC_MAX_INTERFACES}"
+        elif st == KFP_EINVAL:
+            msg = "NULL pointer or non-positive size"
+        else:
+            msg = "device set-up or kernel launch failed"
+        raise KfpError(st, f"kfp_iface_norms_noalloc: {msg}")
 
 
 def kfp_swr_last_error(h: int) -> str:
