@@ -16,12 +16,13 @@
 // Coefficient record of one row, one column class and one pass direction (24 = 3
 // classes x 8 fields):
 //   0: -cp   back-substitution coefficient of step k (eliminated the other way)
-//   1: sign of v_i (integer bits)
-//   2: A  = g (1 - c_i)     3: B = g c_i        (upwind transport, c_i = |v_i| dt/hx)
-//   4: -g a (coupling to the previously eliminated row)
-//   5: g     6: g * 2dt/hv (Robin interface data)
+//   1: A  = g (1 - c_i)     2: B = g c_i        (upwind transport, c_i = |v_i| dt/hx)
+//   3: -g a (coupling to the previously eliminated row)
+//   4: g     5: g * 2dt/hv (Robin interface data)
+//   6: sign of v_i (integer bits)
 //   7: row kind (integer bits: 0 interior, 1 x inflow, 2 v boundary,
 //      3/4 Dirichlet top/bottom, 5/6 Robin top/bottom)
+// Fields 0-3 are read as one 16-byte vector (FP32) or two (FP64).
 // Identity rows (kinds 1-4) carry A = B = -g a = g = 0 (and G = 0), so that with zero
 // boundary data they need no branch; their data, the interface rows and rows whose
 // u^k is recorded are handled in the first and last chunk of a pass (general path).
@@ -112,6 +113,17 @@ struct TmaSmem {
   uint64_t empty[NST];
 };
 
+// Fields 0..3 of a record (ncp, A, B, -g a) as vector loads.
+__device__ __forceinline__ void load_coef4(const double* rc, double& ncp, double& a, double& b, double& hn) {
+  const double2 v0 = *reinterpret_cast<const double2*>(rc);
+  const double2 v1 = *reinterpret_cast<const double2*>(rc + 2);
+  ncp = v0.x; a = v0.y; b = v1.x; hn = v1.y;
+}
+__device__ __forceinline__ void load_coef4(const float* rc, float& ncp, float& a, float& b, float& hn) {
+  const float4 v = *reinterpret_cast<const float4*>(rc);
+  ncp = v.x; a = v.y; b = v.z; hn = v.w;
+}
+
 // Record the outgoing interface data and the overlap values of u^k at row l.
 template <typename T, bool UP>
 __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo& st, int s, int k, int l,
@@ -188,7 +200,7 @@ __device__ __forceinline__ T special_row(const PassArgs<T>& A, const StripInfo& 
 // 2: back-substitute the last step and store u^nt.  FMODE: 0 no forcing, 1 folded
 // constant forcing, 2 one time-dependent term.
 template <typename T, bool UP, int MODE, int FMODE, int NST>
-__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32)
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
 sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const int k) {
   // The dynamic shared-memory base is at least 16-byte aligned, which is what an
   // unswizzled TMA destination needs; using it directly (no integer round trip)
@@ -273,6 +285,22 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
 
   T u_prev = T(0), u_m1 = T(0), u_m2 = T(0), y_prev = T(0);
   const int step = UP ? P : -P;
+  // Elimination chain of the previous interior chunk, deferred so that it runs
+  // interleaved with the back-substitution chain of the next one: two independent
+  // FMA chains keep the FP64 pipe busy.  Its inputs live in registers, so its
+  // shared-memory stage is already released.
+  bool pend = false;
+  T xx[kChunk], hn[kChunk];
+  T* pout = nullptr;
+  auto drain = [&]() {
+#pragma unroll
+    for (int t = 0; t < kChunk; ++t) {
+      y_prev = fma(hn[t], y_prev, xx[t]);
+      if (out_lane) *pout = y_prev;
+      pout += step;
+    }
+    pend = false;
+  };
   for (int c = 0; c < NC; ++c) {
     const int q = c % NST, use = c / NST;
     if (!mbar_wait(&sm.full[q], use & 1)) {
@@ -286,24 +314,38 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     // Strip-end rows (boundary / interface kinds), recorded rows, rows outside the strip
     // and caller boundary data go through the general path; every other chunk is a
     // run of 16 interior rows with no branch.
-    const bool general = X.bc_data || rec_chunk || c == 0 || c == NC - 1;
+    // the upwind side of every row in the chunk (the v = 0 row and chunks that
+    // straddle it go through the general path)
+    const int sg_first = slot_int(sm.rec[q][0][cls * 8 + 6]);
+    const int sg_last = slot_int(sm.rec[q][kChunk - 1][cls * 8 + 6]);
+    const bool general = X.bc_data || rec_chunk || c == 0 || c == NC - 1 || sg_first != sg_last ||
+                         sg_first == 0;
     if (!general) {
-      // Phased chunk: (1) the back-substitution chain u for 16 rows, (2) shuffles and
-      // the terms that do not depend on the previous row, (3) the elimination chain
-      // y.  Each phase is a run of independent or singly chained FMAs, so in-order
-      // issue never waits on a shuffle inside a chain.
+      const int src = lane - sg_first;  // upwind neighbour lane for the whole chunk
       const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
       const int cbase = wl * kOutCols + lane;
+      // (A) back-substitution chain of this chunk, interleaved with the deferred
+      //     elimination chain of the previous chunk
       T uu[kChunk];
+      if (pend) {
 #pragma unroll
-      for (int t = 0; t < kChunk; ++t) {
-        const int r = UP ? t : (kChunk - 1 - t);
-        const T tile = sm.tile[q][r][cbase];
-        if (MODE == 0) {
-          uu[t] = tile;
-        } else {
-          u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile);
-          uu[t] = u_prev;
+        for (int t = 0; t < kChunk; ++t) {
+          const int r = UP ? t : (kChunk - 1 - t);
+          const T tile = sm.tile[q][r][cbase];
+          if (MODE == 0) uu[t] = tile;
+          else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
+          y_prev = fma(hn[t], y_prev, xx[t]);
+          if (out_lane) *pout = y_prev;
+          pout += step;
+        }
+        pend = false;
+      } else {
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) {
+          const int r = UP ? t : (kChunk - 1 - t);
+          const T tile = sm.tile[q][r][cbase];
+          if (MODE == 0) uu[t] = tile;
+          else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
         }
       }
       if (MODE != 0) {
@@ -318,28 +360,26 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
           outT += step;
         }
       } else {
-        T xx[kChunk];
+        // (B) shuffles and the terms that do not depend on the previous row
 #pragma unroll
         for (int t = 0; t < kChunk; ++t) {
           const int r = UP ? t : (kChunk - 1 - t);
           const T* rc = &sm.rec[q][r][cls * 8];
-          const T unb = shfl_val(uu[t], lane - slot_int(rc[1]));
+          T ncp_unused, ca, cb, chn;
+          load_coef4(rc, ncp_unused, ca, cb, chn);
+          const T unb = shfl_val(uu[t], src);
           T gterm;
           if (FMODE == 0) gterm = T(0);
           else if (FMODE == 1) gterm = sm.frc[q][r][cbase];
-          else gterm = (rc[5] * dtak) * sm.frc[q][r][cbase];
-          xx[t] = fma(rc[2], uu[t], fma(rc[3], unb, gterm));
+          else gterm = (rc[4] * dtak) * sm.frc[q][r][cbase];
+          xx[t] = fma(ca, uu[t], fma(cb, unb, gterm));
+          hn[t] = chn;
         }
-        T* out = Ynext + (size_t)(st.rowoff + lf) * P + col;
-#pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
-          const int r = UP ? t : (kChunk - 1 - t);
-          y_prev = fma(sm.rec[q][r][cls * 8 + 4], y_prev, xx[t]);
-          if (out_lane) *out = y_prev;
-          out += step;
-        }
+        pout = Ynext + (size_t)(st.rowoff + lf) * P + col;
+        pend = true;
       }
     } else {
+      if (pend) drain();
 #pragma unroll 1
       for (int t = 0; t < kChunk; ++t) {
         const int r = UP ? t : (kChunk - 1 - t);
@@ -360,13 +400,13 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
             continue;
           }
         }
-        const T unb = shfl_val(u, lane - slot_int(rc[1]));
+        const T unb = shfl_val(u, lane - slot_int(rc[6]));
         T gterm = T(0);
         if (FMODE == 1) gterm = sm.frc[q][r][wl * kOutCols + lane];
-        if (FMODE == 2) gterm = (rc[5] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
-        T y = fma(rc[4], y_prev, fma(rc[2], u, fma(rc[3], unb, gterm)));
+        if (FMODE == 2) gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
+        T y = fma(rc[3], y_prev, fma(rc[1], u, fma(rc[2], unb, gterm)));
         const int kind = slot_int(rc[7]);
-        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[6]);
+        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[5]);
         if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
         y_prev = y;
       }
@@ -374,6 +414,7 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[q]);
   }
+  if (pend) drain();
 }
 
 }  // namespace kfp

@@ -601,12 +601,12 @@ kfp_status build_records(kfp_swr* h, const std::vector<double>& coef, const std:
           T* r = &(*rec_out)[(((size_t)s * 2 + dir) * Lpad + kfp::kRecPad + l) * kfp::kRecW + cls * 8];
           const bool ident = kind >= 1 && kind <= 4;
           r[0] = (T)(-cpB);
-          put_bits(&r[1], vi > 0 ? 1 : (vi < 0 ? -1 : 0));
-          r[2] = ident ? T(0) : (T)(gE * (1.0 - cab));
-          r[3] = ident ? T(0) : (T)(gE * cab);
-          r[4] = ident ? T(0) : (T)(-gE * aE);
-          r[5] = ident ? T(0) : (T)gE;
-          r[6] = (T)(gE * two_dt_hv);
+          r[1] = ident ? T(0) : (T)(gE * (1.0 - cab));
+          r[2] = ident ? T(0) : (T)(gE * cab);
+          r[3] = ident ? T(0) : (T)(-gE * aE);
+          r[4] = ident ? T(0) : (T)gE;
+          r[5] = (T)(gE * two_dt_hv);
+          put_bits(&r[6], vi > 0 ? 1 : (vi < 0 ? -1 : 0));
           put_bits(&r[7], kind);
         }
       }
