@@ -13,7 +13,8 @@ timed region; the state of one step (3 x 68 MB) is larger than L2 (129 MB).
 Extra keys: "roofline" (sweep kernel: FP64 is bound by the FP64 pipe, FP32 by HBM),
 "cpu_baseline" (the CPU oracle on a bounded sample), "e2e" (through the C ABI from
 pinned host buffers, copies included), "clocks" (nvidia-smi during the timed
-region), "variants" (the FP32 form) and "time_to_tol" (wall time to e_mis < 1e-8).
+region), "variants" (the FP32 form) and "time_to_tol" (wall time to e_mis < 1e-8 for
+the plain FP64 form and the mixed-precision form).
 
 --impl reference times the CPU oracle (the reference arm of this repository) on the
 host cores on a bounded sample of the same workload.
@@ -46,6 +47,27 @@ FP64_FLOPS_PER_CELL = 8    # 4 fused multiply-adds: transport (2), elimination (
 BYTES_PER_CELL = {"f64": 24, "f32": 12}  # read y^k, read F, write y^{k+1}
 # FP64 pipe of sm_103a: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
+
+
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_pass_at_scale.md")
+SWEEP_SOURCE = os.path.join(ROOT, "paper_1306_4596_gb300", "csrc", "kfp_sweep_tma.cuh")
+
+
+def profiled_traffic(dtype: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, or None when the
+    sweep kernel's source has changed since those counters were taken."""
+    import hashlib
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        digest = hashlib.sha256(open(SWEEP_SOURCE, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if f"sha256[:16] = {digest}" not in text:
+        return None
+    for line in text.splitlines():
+        if line.startswith(f"traffic_bytes_per_launch {dtype} = "):
+            return int(line.split("=")[1])
+    return None
 
 
 def measured_peaks():
@@ -199,6 +221,7 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP32, time-to-tol and CPU legs")
     ap.add_argument("--cpu-nt", type=int, default=60, help="time steps of the CPU-baseline sample")
+    ap.add_argument("--ttol-iters", type=int, default=400, help="FP64 iteration cap of the time-to-1e-8 run")
     ap.add_argument("--ref-nt", type=int, default=6, help="time steps per reference-arm step")
     ap.add_argument("--nt", type=int, default=None,
                     help="shorter time window (profiling captures only; the JSON line records it)")
@@ -254,15 +277,17 @@ def main():
     if args.precision == "f64":
         achieved = cells_per_pass * FP64_FLOPS_PER_CELL / (avg_pass_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profiled_traffic("f64"),
                     "peak_source": "derived: 152 SMs x 4 x 0.5 DFMA/clk x 2 flops x 2.07 GHz",
-                    "kernel": "sweep_pass_kernel<double>", "avg_launch_ms": avg_pass_ms,
+                    "kernel": "sweep_pass_tma_kernel<double>", "avg_launch_ms": avg_pass_ms,
+                    "algorithmic_per_launch": f"{FP64_FLOPS_PER_CELL} flop x {int(cells_per_pass)} cell-updates",
                     "hbm_view": {"achieved_gbs": cells_per_pass * BYTES_PER_CELL["f64"] / (avg_pass_ms / 1e3) / 1e9,
                                  "peak_gbs": hbm, "peak_source": hbm_label}}
     else:
         achieved = cells_per_pass * BYTES_PER_CELL["f32"] / (avg_pass_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "peak_source": hbm_label, "kernel": "sweep_pass_kernel<float>",
+                    "traffic": profiled_traffic("f32"), "peak_source": hbm_label, "kernel": "sweep_pass_tma_kernel<float>",
+                    "algorithmic_per_launch": f"{BYTES_PER_CELL['f32']} B x {int(cells_per_pass)} cell-updates",
                     "avg_launch_ms": avg_pass_ms}
 
     line = {
@@ -309,18 +334,22 @@ def main():
             var["hbm_frac"] = var["hbm_gbs"] / hbm
         line["variants"] = [var]
 
-        # ---- time to e_mis < 1e-8 -----------------------------------------------------
+        # ---- time to e_mis < 1e-8: plain FP64 vs mixed precision ----------------------
         ttol = {}
-        for prec in ("f64", "f32"):
+        for prec, cap in (("f64", args.ttol_iters), ("mixed", 40)):
             with swr_mod.SWR(prob, prec, inputs_on="device") as s:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                n = s.sweep(60, 1e-8, 1)
+                n = s.sweep(cap, 1e-8, 1)
                 torch.cuda.synchronize()
                 el = time.perf_counter() - t0
                 e = s.error()
-            ttol[prec] = {"seconds": el, "iterations": n, "e_mis": e[0], "reached": bool(e[0] < 1e-8)}
-        line["time_to_tol"] = {"tol": 1e-8, "norm": "e_mis", **ttol}
+                cnt = s.counters()
+            ttol[prec] = {"seconds": el, "fp64_iterations": cnt["fp64_iterations"],
+                          "fp32_iterations": cnt["fp32_iterations"], "e_mis": e[0], "reached": bool(e[0] < 1e-8)}
+        if ttol["f64"]["reached"] and ttol["mixed"]["reached"]:
+            ttol["speedup_mixed_vs_f64"] = ttol["f64"]["seconds"] / ttol["mixed"]["seconds"]
+        line["time_to_tol"] = {"tol": 1e-8, "norm": "e_mis (FP64 sweep)", **ttol}
 
         # ---- CPU oracle on a bounded sample -------------------------------------------
         rate, cells, secs = cpu_oracle_rate(prob, args.cpu_nt)

@@ -59,8 +59,14 @@ typedef enum {
 typedef enum { KFP_DIRICHLET = 0, KFP_ROBIN = 1 } kfp_transmission;
 
 /* Arithmetic of the strip solves.  Interface traces, bands, norms and every array
- * crossing the ABI stay FP64 in all modes. */
-typedef enum { KFP_F64 = 0, KFP_F32 = 1 } kfp_precision;
+ * crossing the ABI stay FP64 in all modes.
+ * KFP_MIXED: defect correction on the interface problem.  Each outer step runs one
+ * FP64 iteration from the current interface data lambda (its norms are the ones
+ * reported; its residual is d = G(lambda) - lambda with G the map of one iteration),
+ * then solves delta = M delta + d (M = the linear part of G) by FP32 iterations of
+ * the homogeneous problem and sets lambda += delta in FP64; the FP32 rounding thus
+ * falls on the correction only.  kfp_swr_sweep's max_iters counts outer steps. */
+typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
 
 /* Flags of kfp_swr_desc.flags */
 #define KFP_FLAG_NO_GRAPH 1u  /* launch every kernel directly instead of replaying a CUDA graph */
@@ -187,6 +193,13 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
  */
 kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx, double dt,
                                    double hx, double* out, void* cuda_stream);
+
+/* Iteration counters (any pointer may be NULL): iterations whose strip solves ran
+ * in FP64 and in FP32 (for KFP_MIXED: outer FP64 steps and inner FP32 correction
+ * iterations), and -- with KFP_FLAG_PROFILE -- the summed device time of the FP32
+ * sweep kernels in milliseconds.  Synchronises.  Errors: KFP_EINVAL, KFP_ECUDA. */
+kfp_status kfp_swr_counters(kfp_swr_t h, long long* fp64_iterations, long long* fp32_iterations,
+                            double* fp32_sweep_ms);
 
 /* Free every resource of the handle (NULL is ignored).  Synchronises its stream. */
 void kfp_swr_destroy(kfp_swr_t h);

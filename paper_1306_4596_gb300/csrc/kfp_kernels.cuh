@@ -273,6 +273,48 @@ exchange_kernel(const double* __restrict__ lam_next, double* __restrict__ lam_in
   last_block_combine(partial, ticket, mx, sm, &scal[1], nullptr);
 }
 
+// Defect correction on the interface problem (mixed precision).  With G the map of
+// one FP64 iteration, the residual of the current interface data lam is
+// d = G(lam) - lam; the correction delta solves delta = M delta + d, where M is the
+// linear part of G, by FP32 iterations of the homogeneous problem; then lam += delta.
+
+// d = lam_next - lam_in (lam_in unchanged), scal[1] = max |d|.
+__global__ void __launch_bounds__(kReduceThreads)
+residual_kernel(const double* __restrict__ lam_next, const double* __restrict__ lam_in,
+                double* __restrict__ d, size_t n, double* partial, unsigned* ticket, double* scal) {
+  double mx = 0.0, sm = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double r = lam_next[e] - lam_in[e];
+    d[e] = r;
+    mx = nan_max(mx, fabs(r));
+  }
+  block_reduce(mx, sm);
+  last_block_combine(partial, ticket, mx, sm, &scal[1], nullptr);
+}
+
+// delta <- M delta + d, where lam_next holds M delta from the homogeneous sweep;
+// scal[1] = max |new delta - old delta|.
+__global__ void __launch_bounds__(kReduceThreads)
+inner_exchange_kernel(const double* __restrict__ lam_next, const double* __restrict__ d,
+                      double* __restrict__ delta, size_t n, double* partial, unsigned* ticket, double* scal) {
+  double mx = 0.0, sm = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double v = lam_next[e] + d[e];
+    mx = nan_max(mx, fabs(v - delta[e]));
+    delta[e] = v;
+  }
+  block_reduce(mx, sm);
+  last_block_combine(partial, ticket, mx, sm, &scal[1], nullptr);
+}
+
+// lam_in += delta
+__global__ void correct_kernel(double* __restrict__ lam_in, const double* __restrict__ delta, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    lam_in[e] += delta[e];
+}
+
 // Error: e_mis = max |lower - upper| over the overlaps, j_l2 = dt hx sum (lower-upper)^2.
 // Also appends (e_mis, e_chg, j_l2) to the device history.
 __global__ void __launch_bounds__(kReduceThreads)

@@ -66,7 +66,7 @@ kfp_status build_geometry(const kfp_swr_desc* d, int nforce, Geometry* g, std::s
     return bad(KFP_EINVAL, "need x1 > x0, v1 > v0, dt > 0");
   if (d->nv % d->nstrips != 0) return bad(KFP_EINVAL, "nstrips must divide nv");
   if (d->tc != KFP_DIRICHLET && d->tc != KFP_ROBIN) return bad(KFP_EINVAL, "unknown transmission");
-  if (d->prec != KFP_F64 && d->prec != KFP_F32) return bad(KFP_EINVAL, "unknown precision");
+  if (d->prec != KFP_F64 && d->prec != KFP_F32 && d->prec != KFP_MIXED) return bad(KFP_EINVAL, "unknown precision");
   if (nforce < 0) return bad(KFP_EINVAL, "nforce < 0");
   const int S = d->nstrips;
   const int w = d->nv / S;
@@ -234,8 +234,16 @@ struct kfp_swr {
   long long iterations = 0;
   std::vector<double> history;  // host copy, 3 per iteration
 
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
+  // mixed precision: the homogeneous FP32 solver of the corrections, the residual
+  // d = G(lam) - lam of the outer (FP64) handle, and the inner handle's view of it
+  kfp_swr* inner = nullptr;
+  double* d_res = nullptr;
+  const double* d_ext = nullptr;
+  long long inner_iterations = 0;
+  int inner_max = 4000;
+  double inner_rtol = 1e-7;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double t_sweep = 0, t_exchange = 0, t_error = 0;
@@ -347,18 +355,31 @@ struct kfp_swr {
     else cudaEventRecord(ev[idx], st);
   }
 
-  // One SWR iteration: sweep, exchange, error.
-  void enqueue_iteration(cudaStream_t st, bool capturing) const {
+  // One SWR iteration: the nt+1 sweep passes, then
+  //   kStandard: exchange (lam_in <- lam_next, e_chg) and error (e_mis, j_l2);
+  //   kResidual: d = lam_next - lam_in (lam_in kept) and error -- the outer FP64 step
+  //              of the mixed-precision form;
+  //   kInner:    delta <- M delta + d on the homogeneous FP32 problem (no error).
+  enum IterKind { kStandard = 0, kResidual = 1, kInner = 2 };
+
+  void enqueue_iteration(cudaStream_t st, bool capturing, int kind) const {
     record(0, st, capturing);
     if (prec == KFP_F64) enqueue_passes<double>(st);
     else enqueue_passes<float>(st);
     record(1, st, capturing);
     if (g.S > 1) {
-      kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
-          lam_next, lam_in, n_trace, partial, tickets + 0, scal);
+      if (kind == kStandard)
+        kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+            lam_next, lam_in, n_trace, partial, tickets + 0, scal);
+      else if (kind == kResidual)
+        kfp::residual_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+            lam_next, lam_in, d_res, n_trace, partial, tickets + 0, scal);
+      else
+        kfp::inner_exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+            lam_next, d_ext, lam_in, n_trace, partial, tickets + 0, scal);
     }
     record(2, st, capturing);
-    if (g.S > 1) {
+    if (g.S > 1 && kind != kInner) {
       kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
           bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
           scal, hist, iter, hist_cap);
@@ -366,27 +387,29 @@ struct kfp_swr {
     record(3, st, capturing);
   }
 
-  kfp_status build_graph() {
-    if (graph_exec) return KFP_OK;
+  kfp_status build_graph(int kind) {
+    if (graph_exec[kind]) return KFP_OK;
     if (!cap_stream) KFP_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     KFP_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration(cap_stream, true);
+    enqueue_iteration(cap_stream, true, kind);
     cudaGraph_t gr = nullptr;
     cudaError_t e = cudaStreamEndCapture(cap_stream, &gr);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(KFP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     }
-    graph = gr;
-    KFP_CUDA_TRY(cudaGraphInstantiate(&graph_exec, graph, 0));
+    graph[kind] = gr;
+    KFP_CUDA_TRY(cudaGraphInstantiate(&graph_exec[kind], graph[kind], 0));
     return KFP_OK;
   }
 
   void drop_graph() {
-    if (graph_exec) cudaGraphExecDestroy(graph_exec);
-    if (graph) cudaGraphDestroy(graph);
-    graph_exec = nullptr;
-    graph = nullptr;
+    for (int k = 0; k < 3; ++k) {
+      if (graph_exec[k]) cudaGraphExecDestroy(graph_exec[k]);
+      if (graph[k]) cudaGraphDestroy(graph[k]);
+      graph_exec[k] = nullptr;
+      graph[k] = nullptr;
+    }
   }
 
   kfp_status ensure_history(int n) {
@@ -398,55 +421,47 @@ struct kfp_swr {
     if (hist) cudaFree(hist);
     hist = h;
     hist_cap = cap;
-    drop_graph();  // the graph captured the old pointer
+    drop_graph();  // the graphs captured the old pointer
     return KFP_OK;
   }
 
-  kfp_status sweep(int max_iters, double tol, int tol_kind, int* iters_done) {
-    if (iters_done) *iters_done = 0;
-    if (max_iters < 0 || (tol_kind != 0 && tol_kind != 1))
-      return fail(KFP_EINVAL, "need max_iters >= 0 and tol_kind in {0, 1}");
-    if (max_iters == 0) return KFP_OK;
-    kfp_status rc = ensure_history(max_iters);
-    if (rc) return rc;
-    KFP_CUDA_TRY(cudaMemsetAsync(iter, 0, sizeof(int), stream));
-    const bool use_graph = !(flags & KFP_FLAG_NO_GRAPH);
-    if (use_graph) {
-      rc = build_graph();
+  // Launch one iteration of the given kind (graph replay or direct launches) and,
+  // with KFP_FLAG_PROFILE, add its kernel times.
+  kfp_status launch_iteration(int kind) {
+    if (!(flags & KFP_FLAG_NO_GRAPH)) {
+      kfp_status rc = build_graph(kind);
       if (rc) return rc;
+      KFP_CUDA_TRY(cudaGraphLaunch(graph_exec[kind], stream));
+    } else {
+      enqueue_iteration(stream, false, kind);
+      KFP_CUDA_TRY(cudaGetLastError());
     }
-    const bool check = tol > 0;
-    const bool profile = (flags & KFP_FLAG_PROFILE) != 0;
-    int done = 0;
-    bool converged = false;
-    for (int it = 0; it < max_iters; ++it) {
-      if (use_graph) {
-        KFP_CUDA_TRY(cudaGraphLaunch(graph_exec, stream));
-      } else {
-        enqueue_iteration(stream, false);
-        KFP_CUDA_TRY(cudaGetLastError());
-      }
-      ++done;
-      if (profile) {
-        KFP_CUDA_TRY(cudaEventSynchronize(ev[3]));
-        float a = 0, b = 0, c = 0;
-        KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
-        KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
-        KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
-        t_sweep += a; t_exchange += b; t_error += c;
-      }
-      if (check && g.S > 1) {
-        KFP_CUDA_TRY(cudaMemcpyAsync(host_scal, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, stream));
-        KFP_CUDA_TRY(cudaStreamSynchronize(stream));
-        const double v = tol_kind == 0 ? host_scal[1] : host_scal[0];
-        if (!std::isfinite(host_scal[0]) || !std::isfinite(host_scal[1]) || !std::isfinite(host_scal[2])) {
-          rc = fail(KFP_ENUMERIC, "non-finite interface norm at iteration %lld", iterations + done);
-          break;
-        }
-        if (v < tol) { converged = true; break; }
-      }
+    if (flags & KFP_FLAG_PROFILE) {
+      KFP_CUDA_TRY(cudaEventSynchronize(ev[3]));
+      float a = 0, b = 0, c = 0;
+      KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+      KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+      KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
+      t_sweep += a; t_exchange += b; t_error += c;
     }
-    // pull this call's history
+    return KFP_OK;
+  }
+
+  kfp_status read_scalars() {
+    KFP_CUDA_TRY(cudaMemcpyAsync(host_scal, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, stream));
+    KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+    return KFP_OK;
+  }
+
+  kfp_status check_flag() {
+    if (!use_tma) return KFP_OK;
+    int f = 0;
+    KFP_CUDA_TRY(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) return fail(KFP_ETIMEOUT, "a bounded wait in the sweep kernel expired");
+    return KFP_OK;
+  }
+
+  kfp_status pull_history(int done) {
     if (g.S > 1) {
       std::vector<double> h((size_t)3 * done);
       KFP_CUDA_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * 3 * (size_t)std::min(done, hist_cap),
@@ -457,15 +472,44 @@ struct kfp_swr {
       KFP_CUDA_TRY(cudaStreamSynchronize(stream));
       history.insert(history.end(), (size_t)3 * done, 0.0);
     }
+    return KFP_OK;
+  }
+
+  kfp_status sweep(int max_iters, double tol, int tol_kind, int* iters_done) {
+    if (iters_done) *iters_done = 0;
+    if (max_iters < 0 || (tol_kind != 0 && tol_kind != 1))
+      return fail(KFP_EINVAL, "need max_iters >= 0 and tol_kind in {0, 1}");
+    if (max_iters == 0) return KFP_OK;
+    if (inner) return sweep_mixed(max_iters, tol, tol_kind, iters_done);
+    kfp_status rc = ensure_history(max_iters);
+    if (rc) return rc;
+    KFP_CUDA_TRY(cudaMemsetAsync(iter, 0, sizeof(int), stream));
+    const bool check = tol > 0;
+    int done = 0;
+    bool converged = false;
+    for (int it = 0; it < max_iters; ++it) {
+      rc = launch_iteration(kStandard);
+      if (rc) return rc;
+      ++done;
+      if (check && g.S > 1) {
+        rc = read_scalars();
+        if (rc) return rc;
+        const double v = tol_kind == 0 ? host_scal[1] : host_scal[0];
+        if (!std::isfinite(host_scal[0]) || !std::isfinite(host_scal[1]) || !std::isfinite(host_scal[2])) {
+          rc = fail(KFP_ENUMERIC, "non-finite interface norm at iteration %lld", iterations + done);
+          break;
+        }
+        if (v < tol) { converged = true; break; }
+      }
+    }
+    kfp_status rh = pull_history(done);
+    if (rh) return rh;
     KFP_CUDA_TRY(cudaGetLastError());
     iterations += done;
     if (iters_done) *iters_done = done;
     if (rc) return rc;
-    if (use_tma) {
-      int f = 0;
-      KFP_CUDA_TRY(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
-      if (f) return fail(KFP_ETIMEOUT, "a bounded wait in the sweep kernel expired");
-    }
+    rc = check_flag();
+    if (rc) return rc;
     if (g.S > 1) {
       const double* last = &history[history.size() - 3];
       if (!std::isfinite(last[0]) || !std::isfinite(last[1]) || !std::isfinite(last[2]))
@@ -476,13 +520,83 @@ struct kfp_swr {
     return KFP_OK;
   }
 
+  // Mixed precision: defect correction on the interface problem.  Each outer step
+  // runs one FP64 iteration from the current interface data lam (its overlap
+  // mismatch e_mis and residual d = G(lam) - lam are the reported norms), then
+  // solves delta = M delta + d with FP32 iterations of the homogeneous problem
+  // (zero data; only the interface data delta drive it) and sets lam += delta in
+  // FP64.  The FP32 rounding then sits on the correction, not on lam.  max_iters
+  // counts outer (FP64) steps; the inner loop stops when its change falls below
+  // inner_rtol * |d| or stops decreasing (FP32 floor), at most inner_max steps.
+  kfp_status sweep_mixed(int max_outer, double tol, int tol_kind, int* iters_done) {
+    kfp_status rc = ensure_history(max_outer);
+    if (rc) return rc;
+    KFP_CUDA_TRY(cudaMemsetAsync(iter, 0, sizeof(int), stream));
+    KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+    int done = 0;
+    bool converged = false;
+    const int blocks = reduce_blocks;
+    for (int outer = 0; outer < max_outer; ++outer) {
+      rc = launch_iteration(kResidual);
+      if (rc) break;
+      ++done;
+      rc = read_scalars();
+      if (rc) break;
+      if (!std::isfinite(host_scal[0]) || !std::isfinite(host_scal[1]) || !std::isfinite(host_scal[2])) {
+        rc = fail(KFP_ENUMERIC, "non-finite interface norm at outer step %lld", iterations + done);
+        break;
+      }
+      const double metric = tol_kind == 0 ? host_scal[1] : host_scal[0];
+      if (tol > 0 && metric < tol) { converged = true; break; }
+      if (outer == max_outer - 1) break;  // the last FP64 step is a measurement
+      const double dnorm = host_scal[1];
+      if (!(dnorm > 0)) { converged = tol > 0; break; }
+      // inner FP32 iterations: delta_0 = d, delta <- M delta + d
+      KFP_CUDA_TRY(cudaMemcpyAsync(inner->lam_in, d_res, sizeof(double) * n_trace, cudaMemcpyDeviceToDevice,
+                                   stream));
+      double best = INFINITY;
+      int since_best = 0, j = 0;
+      for (; j < inner_max; ++j) {
+        rc = inner->launch_iteration(kInner);
+        if (rc) { last_error = inner->last_error; break; }
+        rc = inner->read_scalars();
+        if (rc) { last_error = inner->last_error; break; }
+        const double chg = inner->host_scal[1];
+        if (!std::isfinite(chg)) { rc = fail(KFP_ENUMERIC, "non-finite correction"); break; }
+        if (chg < inner_rtol * dnorm) { ++j; break; }
+        if (chg < 0.5 * best) { best = chg; since_best = 0; }
+        else if (++since_best >= 25) { ++j; break; }  // stalled at FP32 resolution
+      }
+      if (rc) break;
+      inner_iterations += j;
+      kfp::correct_kernel<<<blocks, 256, 0, stream>>>(lam_in, inner->lam_in, n_trace);
+      KFP_CUDA_TRY(cudaGetLastError());
+    }
+    kfp_status rh = pull_history(done);
+    if (rh) return rh;
+    iterations += done;
+    if (iters_done) *iters_done = done;
+    if (rc) return rc;
+    rc = check_flag();
+    if (!rc) rc = inner->check_flag();
+    if (rc) return rc;
+    if (tol > 0 && !converged)
+      return fail(KFP_ENOTCONV, "tolerance %g not reached in %d outer steps", tol, done);
+    return KFP_OK;
+  }
+
   void release() {
+    if (inner) {
+      inner->release();
+      delete inner;
+      inner = nullptr;
+    }
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
-                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage};
+                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage, d_res};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (host_scal) cudaFreeHost(host_scal);
@@ -820,6 +934,52 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
 #undef TRY
 }
 
+// Mixed precision: the FP32 solver of the homogeneous problem (zero initial data,
+// forcing and boundary data; only its interface data drive it) that computes the
+// corrections, sharing the outer handle's stream and reading its residual.
+kfp_status create_inner(kfp_swr* h, const kfp_swr_desc* d) {
+  const Geometry& g = h->g;
+  if (g.S < 2) return KFP_OK;  // one strip: no interface problem, FP64 steps only
+  kfp_status rc = alloc(h, (void**)&h->d_res, sizeof(double) * h->n_trace);
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->d_res, 0, sizeof(double) * h->n_trace, h->stream));
+  double* zeros = nullptr;
+  const size_t nu = (size_t)(g.nv + 1) * (g.nx + 1);
+  rc = alloc(h, (void**)&zeros, sizeof(double) * nu);
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemsetAsync(zeros, 0, sizeof(double) * nu, h->stream));
+  kfp_swr_desc di = *d;
+  di.prec = KFP_F32;
+  kfp_swr_problem pi;
+  std::memset(&pi, 0, sizeof pi);
+  pi.on_device = 1;
+  pi.u0 = zeros;
+  kfp_swr* in = new (std::nothrow) kfp_swr();
+  if (!in) {
+    cudaFree(zeros);
+    return h->fail(KFP_ENOMEM, "host allocation failed");
+  }
+  std::string err;
+  rc = build_geometry(&di, 0, &in->g, &err);
+  if (!rc) {
+    in->prec = KFP_F32;
+    in->flags = d->flags;
+    in->stream = h->stream;
+    rc = create_impl(in, &di, &pi);
+    if (rc) err = in->last_error;
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(zeros);
+  if (rc) {
+    in->release();
+    delete in;
+    return h->fail(rc, "inner FP32 solver: %s", err.c_str());
+  }
+  in->d_ext = h->d_res;
+  h->inner = in;
+  return KFP_OK;
+}
+
 kfp_status copy_out(kfp_swr* h, double* dst, const double* src, size_t n, int dst_on_device) {
   cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * n,
                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -865,10 +1025,11 @@ kfp_status kfp_swr_create(const kfp_swr_desc* desc, const kfp_swr_problem* prob,
     delete h;
     return rc;
   }
-  h->prec = desc->prec;
+  h->prec = desc->prec == KFP_MIXED ? KFP_F64 : desc->prec;
   h->flags = desc->flags;
   h->stream = (cudaStream_t)cuda_stream;
   rc = create_impl(h, desc, prob);
+  if (!rc && desc->prec == KFP_MIXED) rc = create_inner(h, desc);
   if (rc) {
     g_create_error = h->last_error;
     cudaStreamSynchronize(h->stream);
@@ -956,6 +1117,17 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
   if (sweep_ms) *sweep_ms = h->t_sweep;
   if (exchange_ms) *exchange_ms = h->t_exchange;
   if (error_ms) *error_ms = h->t_error;
+  return KFP_OK;
+}
+
+kfp_status kfp_swr_counters(kfp_swr_t h, long long* fp64_iterations, long long* fp32_iterations,
+                            double* fp32_sweep_ms) {
+  if (!h) return KFP_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(KFP_ECUDA, "sync failed");
+  const bool f64 = h->prec == KFP_F64;
+  if (fp64_iterations) *fp64_iterations = f64 ? h->iterations : 0;
+  if (fp32_iterations) *fp32_iterations = f64 ? h->inner_iterations : h->iterations;
+  if (fp32_sweep_ms) *fp32_sweep_ms = h->inner ? h->inner->t_sweep : (f64 ? 0.0 : h->t_sweep);
   return KFP_OK;
 }
 

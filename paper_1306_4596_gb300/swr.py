@@ -21,12 +21,13 @@ KFP_OK, KFP_EINVAL, KFP_ECFL, KFP_ENOMEM, KFP_ECUDA, KFP_ENOTCONV, KFP_ENUMERIC,
 STATUS_NAMES = {0: "KFP_OK", 1: "KFP_EINVAL", 2: "KFP_ECFL", 3: "KFP_ENOMEM", 4: "KFP_ECUDA",
                 5: "KFP_ENOTCONV", 6: "KFP_ENUMERIC", 7: "KFP_ETIMEOUT", 8: "KFP_ENOTSUP"}
 KFP_DIRICHLET, KFP_ROBIN = 0, 1
-KFP_F64, KFP_F32 = 0, 1
+KFP_F64, KFP_F32, KFP_MIXED = 0, 1, 2
+PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
 KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC = 1, 2, 4
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
-            "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc")
+            "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters")
 KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -77,6 +78,8 @@ def load(rebuild: bool = False):
             lib.kfp_swr_bands.argtypes = [vp, i, i, vp, i]
             lib.kfp_swr_solution.argtypes = [vp, vp, i]
             lib.kfp_swr_stats.argtypes = [vp, llp, llp, ip, _dp, _dp, _dp]
+            lib.kfp_swr_counters.argtypes = [vp, llp, llp, _dp]
+            lib.kfp_swr_counters.restype = ctypes.c_int
             lib.kfp_swr_destroy.argtypes = [vp]
             lib.kfp_swr_destroy.restype = None
             lib.kfp_swr_last_error.argtypes = [vp]
@@ -150,6 +153,13 @@ def kfp_swr_stats(h: int) -> dict:
                                    *[ctypes.byref(x) for x in t]))
     return {"iterations": it.value, "cell_updates_per_iter": cells.value, "launches_per_iter": launches.value,
             "sweep_ms": t[0].value, "exchange_ms": t[1].value, "error_ms": t[2].value}
+
+
+def kfp_swr_counters(h: int) -> dict:
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    t = ctypes.c_double()
+    _check(h, load().kfp_swr_counters(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
+    return {"fp64_iterations": a.value, "fp32_iterations": b.value, "fp32_sweep_ms": t.value}
 
 
 def kfp_swr_destroy(h: int) -> None:
@@ -229,7 +239,7 @@ class SWR:
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
                                  self._p.ctypes.data if self._p is not None else None,
                                  self._q.ctypes.data if self._q is not None else None,
-                                 KFP_F64 if precision == "f64" else KFP_F32, flags)
+                                 PRECISIONS[precision], flags)
         nforce = int(prob.f_time.shape[0])
         self.cdata = kfp_swr_problem(1 if on_dev else 0, put(prob.u0), nforce, put(prob.f_time),
                                      put(prob.f_space), put(prob.bc_xin), put(prob.bc_v), put(prob.lam0))
@@ -280,6 +290,9 @@ class SWR:
 
     def stats(self) -> dict:
         return kfp_swr_stats(self.h)
+
+    def counters(self) -> dict:
+        return kfp_swr_counters(self.h)
 
     def close(self) -> None:
         if getattr(self, "h", None):
