@@ -527,7 +527,8 @@ struct kfp_swr {
   // (zero data; only the interface data delta drive it) and sets lam += delta in
   // FP64.  The FP32 rounding then sits on the correction, not on lam.  max_iters
   // counts outer (FP64) steps; the inner loop stops when its change falls below
-  // inner_rtol * |d| or stops decreasing (FP32 floor), at most inner_max steps.
+  // eta * |d| -- eta = inner_rtol, or looser when the target tolerance is near --
+  // or stops decreasing (FP32 floor), at most inner_max steps.
   kfp_status sweep_mixed(int max_outer, double tol, int tol_kind, int* iters_done) {
     kfp_status rc = ensure_history(max_outer);
     if (rc) return rc;
@@ -551,6 +552,10 @@ struct kfp_swr {
       if (outer == max_outer - 1) break;  // the last FP64 step is a measurement
       const double dnorm = host_scal[1];
       if (!(dnorm > 0)) { converged = tol > 0; break; }
+      // Solve the correction only as far as the target needs: the remaining error
+      // must drop by about tol / metric (with margin), never below FP32 resolution.
+      double eta = inner_rtol;
+      if (tol > 0) eta = std::min(0.5, std::max(inner_rtol, 0.2 * tol / metric));
       // inner FP32 iterations: delta_0 = d, delta <- M delta + d
       KFP_CUDA_TRY(cudaMemcpyAsync(inner->lam_in, d_res, sizeof(double) * n_trace, cudaMemcpyDeviceToDevice,
                                    stream));
@@ -563,7 +568,7 @@ struct kfp_swr {
         if (rc) { last_error = inner->last_error; break; }
         const double chg = inner->host_scal[1];
         if (!std::isfinite(chg)) { rc = fail(KFP_ENUMERIC, "non-finite correction"); break; }
-        if (chg < inner_rtol * dnorm) { ++j; break; }
+        if (chg < eta * dnorm) { ++j; break; }
         if (chg < 0.5 * best) { best = chg; since_best = 0; }
         else if (++since_best >= 25) { ++j; break; }  // stalled at FP32 resolution
       }
