@@ -201,6 +201,49 @@ kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int ove
 kfp_status kfp_swr_counters(kfp_swr_t h, long long* fp64_iterations, long long* fp32_iterations,
                             double* fp32_sweep_ms);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent problems (uneven grids, strip counts, Robin
+ * parameters and step counts) swept together.  Every time step of every problem is
+ * one work unit per (strip, block of 120 columns); one launch per time step runs the
+ * units of all problems that have that step, and one iteration (all launches plus
+ * the per-problem exchange and error reductions) replays as one CUDA graph.  The
+ * method per problem is exactly that of kfp_swr_sweep (Section 6.3, parallel form).
+ * ------------------------------------------------------------------------- */
+typedef struct kfp_batch* kfp_batch_t;
+
+/* Create count problems (descs[i], probs[i] as for kfp_swr_create) on one stream.
+ * All problems use the same precision, KFP_F64 or KFP_F32, and at most one forcing
+ * term.  Errors: KFP_EINVAL, KFP_ECFL, KFP_ENOMEM, KFP_ECUDA, KFP_ENOTSUP (mixed
+ * precision or two or more forcing terms); the message is kfp_batch_last_error(NULL). */
+kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* probs, int count, void* cuda_stream,
+                            kfp_batch_t* out);
+
+/* Launch shape: blocks_per_sm = 0 runs one block per work unit; > 0 runs a persistent
+ * grid of blocks_per_sm x (number of SMs) blocks that walk the unit list.  unit_order
+ * 0 lists the units of each step count by decreasing work, 1 keeps problem order.
+ * Results do not depend on either choice.  Synchronises.  Errors: KFP_EINVAL. */
+kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order);
+
+/* Run iterations of every problem, as kfp_swr_sweep; with tol > 0 stop when every
+ * problem's chosen norm is below tol. */
+kfp_status kfp_batch_sweep(kfp_batch_t b, int max_iters, double tol, int tol_kind, int* iters_done);
+
+/* Handle of problem `index`, for kfp_swr_traces / error / bands / solution / stats.
+ * It stays owned by the batch: do not destroy it. */
+kfp_status kfp_batch_instance(kfp_batch_t b, int index, kfp_swr_t* h);
+
+/* Iterations run, cell-updates per iteration summed over the problems, and (with
+ * KFP_FLAG_PROFILE in descs[0].flags) the summed device time of the sweep launches
+ * and of the reductions, in milliseconds.  Synchronises. */
+kfp_status kfp_batch_stats(kfp_batch_t b, long long* iterations, long long* cell_updates_per_iter, double* sweep_ms,
+                           double* reduce_ms);
+
+/* Free the batch and all its problems (NULL is ignored). */
+void kfp_batch_destroy(kfp_batch_t b);
+
+/* Message of the last error on b, or of the last failed kfp_batch_create (b = NULL). */
+const char* kfp_batch_last_error(kfp_batch_t b);
+
 /* Free every resource of the handle (NULL is ignored).  Synchronises its stream. */
 void kfp_swr_destroy(kfp_swr_t h);
 

@@ -1,0 +1,81 @@
+"""Launch-shape autotuner for the batched sweep.
+
+The batched sweep has two launch knobs that do not change results:
+``blocks_per_sm`` (0 = one block per work unit, the hardware block scheduler
+balances the load; k > 0 = a persistent grid of k blocks per SM walking the unit
+list) and ``unit_order`` (units of each step count by decreasing work, or in
+problem order).  ``tune`` times one SWR iteration of the actual batch for every
+candidate with CUDA events on the batch's stream and keeps the fastest; the choice
+is cached per batch signature (precision and the sorted problem shapes) in a JSON
+file under ``$KFP_SWR_CACHE`` (default ``~/.cache/kfp_swr``), so a later batch of
+the same shapes skips the timing.  Tuning iterations are real SWR iterations of
+the batch (they advance it).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import Dict, Iterable, Optional, Tuple
+
+CANDIDATES: Tuple[Tuple[int, int], ...] = ((0, 0), (0, 1), (1, 0), (1, 1))
+
+
+def cache_path() -> str:
+    root = os.environ.get("KFP_SWR_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "kfp_swr"))
+    return os.path.join(root, "autotune.json")
+
+
+def signature(probs, precision: str) -> str:
+    shapes = sorted((p.nx, p.nv, p.nstrips, p.overlap, p.nt, int(p.f_time.shape[0])) for p in probs)
+    h = hashlib.sha256(json.dumps([precision, shapes]).encode()).hexdigest()[:24]
+    return f"{precision}:{len(shapes)}:{h}"
+
+
+def _load_cache() -> Dict[str, dict]:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(cache: Dict[str, dict]) -> None:
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    os.replace(tmp, path)
+
+
+def tune(batch, precision: str, candidates: Iterable[Tuple[int, int]] = CANDIDATES, use_cache: bool = True,
+         repeats: int = 1) -> dict:
+    """Pick and apply the fastest (blocks_per_sm, unit_order) for this batch."""
+    import torch
+
+    key = signature(batch.probs, precision)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        best = cache[key]
+        batch.configure(best["blocks_per_sm"], best["unit_order"])
+        return {**best, "cached": True}
+    stream = batch.stream
+    timings = []
+    for bps, order in candidates:
+        batch.configure(bps, order)
+        batch.sweep(1)  # graph capture and warm-up
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        batch.sweep(repeats)
+        end.record(stream)
+        end.synchronize()
+        timings.append({"blocks_per_sm": bps, "unit_order": order, "ms": start.elapsed_time(end) / repeats})
+    best = min(timings, key=lambda t: t["ms"])
+    batch.configure(best["blocks_per_sm"], best["unit_order"])
+    result = {"blocks_per_sm": best["blocks_per_sm"], "unit_order": best["unit_order"], "ms": best["ms"],
+              "candidates": timings}
+    if use_cache:
+        cache[key] = result
+        _store_cache(cache)
+    return {**result, "cached": False}

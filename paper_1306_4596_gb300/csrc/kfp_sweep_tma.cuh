@@ -199,23 +199,8 @@ __device__ __forceinline__ T special_row(const PassArgs<T>& A, const StripInfo& 
 // MODE 0: eliminate step 1 from u^0; 1: back-substitute step k, eliminate step k+1;
 // 2: back-substitute the last step and store u^nt.  FMODE: 0 no forcing, 1 folded
 // constant forcing, 2 one time-dependent term.
-template <typename T, bool UP, int MODE, int FMODE, int NST>
-__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
-sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const int k) {
-  // The dynamic shared-memory base is at least 16-byte aligned, which is what an
-  // unswizzled TMA destination needs; using it directly (no integer round trip)
-  // keeps every tile access a shared-memory load.
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
-  const PassArgs<T>& A = X.p;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.y;
-  const StripInfo st = A.strips[s];
-  const int L = st.L;
-  const int NC = (L + kChunk - 1) / kChunk;
-  constexpr bool kUseForce = (MODE != 2) && (FMODE != 0);
-  const int dir = UP ? 0 : 1;
-
+template <typename T, int NST>
+__device__ __forceinline__ void init_ring(TmaSmem<T, NST>& sm) {
   if (threadIdx.x == 0) {
     for (int q = 0; q < NST; ++q) {
       mbar_init(&sm.full[q], 1);
@@ -224,19 +209,36 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+}
+
+// One work unit: strip s, column block bx (4 warps = 120 output columns) of one
+// problem, for pass k.  Ring slots continue from chunk number cbase (so a block can
+// run several units back to back).  Returns false if a bounded wait expired.
+template <typename T, bool UP, int MODE, int FMODE, int NST>
+__device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
+                                          const int bx, TmaSmem<T, NST>& sm, const unsigned cbase) {
+  const PassArgs<T>& A = X.p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const StripInfo st = A.strips[s];
+  const int L = st.L;
+  const int NC = (L + kChunk - 1) / kChunk;
+  constexpr bool kUseForce = (MODE != 2) && (FMODE != 0);
+  const int dir = UP ? 0 : 1;
 
   auto chunk_l0 = [&](int c) { return UP ? c * kChunk : L - (c + 1) * kChunk; };
 
   if (warp == kWarpsPerBlock) {
     // ------------------------------ producer ------------------------------
     if (lane == 0) {
-      const int x0 = blockIdx.x * (kWarpsPerBlock * kOutCols);
+      const int x0 = bx * (kWarpsPerBlock * kOutCols);
       const unsigned bytes = (unsigned)(sizeof(T) * (kChunk * kBoxW * (kUseForce ? 2 : 1) + kChunk * kRecW));
       const int cur = k & 1;
       bool ok = true;
       int issued = 0;
       for (int c = 0; c < NC; ++c) {
-        const int q = c % NST, use = c / NST;
+        const unsigned g = cbase + (unsigned)c;
+        const int q = (int)(g % NST);
+        const unsigned use = g / NST;
         if (use > 0 && !mbar_wait(&sm.empty[q], (use - 1) & 1)) { ok = false; break; }
         const int l0 = chunk_l0(c);
         mbar_expect_tx(&sm.full[q], bytes);
@@ -252,16 +254,19 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
       if (!ok) {
         atomicExch(X.flag, 1);
         // drain: wait (bounded) for every stage that still has copies in flight
-        for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c)
-          (void)mbar_wait(&sm.full[c % NST], (c / NST) & 1);
+        for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c) {
+          const unsigned g = cbase + (unsigned)c;
+          (void)mbar_wait(&sm.full[g % NST], (g / NST) & 1);
+        }
+        return false;
       }
     }
-    return;
+    return true;
   }
 
   // ------------------------------ consumers ------------------------------
   const int wl = warp;
-  const int w = blockIdx.x * kWarpsPerBlock + wl;
+  const int w = bx * kWarpsPerBlock + wl;
   const bool warp_live = w < A.W;
   const int m = w * kOutCols - 1 + lane;
   const int col = m + 1;
@@ -302,10 +307,11 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     pend = false;
   };
   for (int c = 0; c < NC; ++c) {
-    const int q = c % NST, use = c / NST;
-    if (!mbar_wait(&sm.full[q], use & 1)) {
+    const unsigned g = cbase + (unsigned)c;
+    const int q = (int)(g % NST);
+    if (!mbar_wait(&sm.full[q], (g / NST) & 1)) {
       atomicExch(X.flag, 1);
-      return;
+      return false;
     }
     const int l0 = chunk_l0(c);
     const int l1 = l0 + kChunk - 1;
@@ -415,6 +421,67 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
     if (lane == 0) mbar_arrive(&sm.empty[q]);
   }
   if (pend) drain();
+  return true;
+}
+
+// The dynamic shared-memory base is at least 16-byte aligned, which is what an
+// unswizzled TMA destination needs; using it directly (no integer round trip) keeps
+// every tile access a shared-memory load.
+template <typename T, bool UP, int MODE, int FMODE, int NST>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const int k) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  init_ring(sm);
+  (void)pass_unit<T, UP, MODE, FMODE, NST>(maps, X, k, blockIdx.y, blockIdx.x, sm, 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent problems in one launch per time step.
+// ---------------------------------------------------------------------------
+
+struct BatchUnit {
+  int inst, strip, bx, nc;  // problem, strip, column block, chunks of the strip
+};
+
+template <typename T>
+struct BatchProblem {
+  TmaMaps maps;    // 64-byte aligned tensor maps of this problem (global memory)
+  TmaArgs<T> args;
+  int nt, fmode;
+};
+
+// Units u = blockIdx.x, blockIdx.x + gridDim.x, ...: with gridDim.x = number of units
+// every block runs one unit; with a smaller grid the blocks are persistent and walk
+// the list (sorted by decreasing work on the host).  The pass mode of a unit follows
+// from k and its problem's nt: 0 at k = 0, 2 at k = nt, skipped beyond.
+template <typename T, bool UP, int NST>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+batch_pass_kernel(const BatchProblem<T>* __restrict__ probs, const BatchUnit* __restrict__ units, const int nunits,
+                  const int k) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  init_ring(sm);
+  unsigned cbase = 0;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const BatchUnit un = units[u];
+    const BatchProblem<T>& bp = probs[un.inst];
+    const int nt = bp.nt;
+    if (k > nt) continue;
+    const int mode = (k == 0) ? 0 : (k == nt ? 2 : 1);
+    bool ok = true;
+#define KFP_UNIT(M, F) ok = pass_unit<T, UP, M, F, NST>(bp.maps, bp.args, k, un.strip, un.bx, sm, cbase)
+    if (mode == 1) {
+      if (bp.fmode == 1) KFP_UNIT(1, 1); else if (bp.fmode == 0) KFP_UNIT(1, 0); else KFP_UNIT(1, 2);
+    } else if (mode == 0) {
+      if (bp.fmode == 1) KFP_UNIT(0, 1); else if (bp.fmode == 0) KFP_UNIT(0, 0); else KFP_UNIT(0, 2);
+    } else {
+      KFP_UNIT(2, 0);  // the last pass reads no forcing
+    }
+#undef KFP_UNIT
+    if (!ok) return;
+    cbase += (unsigned)un.nc;
+  }
 }
 
 }  // namespace kfp

@@ -315,12 +315,7 @@ struct kfp_swr {
   template <typename T, int FM>
   void enqueue_passes_tma(cudaStream_t st) const {
     constexpr int NST = tma_stages<T>();
-    kfp::TmaArgs<T> X;
-    X.p = pass_args<T>();
-    X.rows = g.rows;
-    X.Lpad = Lpad;
-    X.flag = flag;
-    X.bc_data = (bc_xin || bc_v) ? 1 : 0;
+    const kfp::TmaArgs<T> X = tma_args<T>();
     const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
     const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
     const size_t sm = tma_smem_bytes<T>();
@@ -385,6 +380,27 @@ struct kfp_swr {
           scal, hist, iter, hist_cap);
     }
     record(3, st, capturing);
+  }
+
+  // Exchange + error of one standard iteration (used by the batched form).
+  void enqueue_reductions(cudaStream_t st) const {
+    if (g.S < 2) return;
+    kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(lam_next, lam_in, n_trace, partial,
+                                                                          tickets + 0, scal);
+    kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+        bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1, scal, hist, iter,
+        hist_cap);
+  }
+
+  template <typename T>
+  kfp::TmaArgs<T> tma_args() const {
+    kfp::TmaArgs<T> X;
+    X.p = pass_args<T>();
+    X.rows = g.rows;
+    X.Lpad = Lpad;
+    X.flag = flag;
+    X.bc_data = (bc_xin || bc_v) ? 1 : 0;
+    return X;
   }
 
   kfp_status build_graph(int kind) {
@@ -997,6 +1013,230 @@ kfp_status copy_out(kfp_swr* h, double* dst, const double* src, size_t n, int ds
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Batched form: independent problems swept together, one launch per time step
+// ---------------------------------------------------------------------------
+
+struct kfp_batch {
+  std::vector<kfp_swr*> inst;
+  kfp_precision prec = KFP_F64;
+  cudaStream_t stream = nullptr;
+  void* probs_dev = nullptr;
+  kfp::BatchUnit* units_dev = nullptr;
+  std::vector<kfp::BatchUnit> units;   // host copy, in launch order
+  std::vector<int> active_prefix;      // units active in pass k = prefix length
+  int max_nt = 0, sms = 1;
+  int blocks_per_sm = 0;               // 0: one block per unit; > 0: persistent grid
+  int unit_order = 0;                  // 0: by decreasing work; 1: round-robin over problems
+  long long iterations = 0, cells_per_iter = 0;
+  double t_sweep = 0, t_reduce = 0;
+  unsigned flags = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  std::string last_error;
+
+  kfp_status fail(kfp_status c, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    last_error = buf;
+    return c;
+  }
+
+  template <typename T>
+  static constexpr int nst() { return kfp_swr::tma_stages<T>(); }
+
+  // Order the units: problems with more steps first (so the units of pass k are a
+  // prefix), then by decreasing work or round-robin over problems.
+  void order_units() {
+    std::stable_sort(units.begin(), units.end(), [&](const kfp::BatchUnit& a, const kfp::BatchUnit& b) {
+      const int na = inst[a.inst]->g.nt, nb = inst[b.inst]->g.nt;
+      if (na != nb) return na > nb;
+      if (unit_order == 0) return a.nc > b.nc;
+      return false;
+    });
+    active_prefix.assign(max_nt + 1, 0);
+    for (int k = 0; k <= max_nt; ++k) {
+      int n = 0;
+      while (n < (int)units.size() && inst[units[n].inst]->g.nt >= k) ++n;
+      active_prefix[k] = n;
+    }
+  }
+
+  template <typename T>
+  void enqueue_passes(cudaStream_t st) const {
+    constexpr int NST = nst<T>();
+    const size_t sm = kfp_swr::tma_smem_bytes<T>();
+    const auto* probs = (const kfp::BatchProblem<T>*)probs_dev;
+    for (int k = 0; k <= max_nt; ++k) {
+      const int n = active_prefix[k];
+      if (n == 0) continue;
+      const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
+      if (k & 1) kfp::batch_pass_kernel<T, false, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(probs, units_dev, n, k);
+      else       kfp::batch_pass_kernel<T, true, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(probs, units_dev, n, k);
+    }
+  }
+
+  void enqueue_iteration(cudaStream_t st, bool capturing) const {
+    auto rec = [&](int i) {
+      if (!(flags & KFP_FLAG_PROFILE)) return;
+      if (capturing) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+      else cudaEventRecord(ev[i], st);
+    };
+    rec(0);
+    if (prec == KFP_F64) enqueue_passes<double>(st);
+    else enqueue_passes<float>(st);
+    rec(1);
+    for (kfp_swr* h : inst) h->enqueue_reductions(st);
+    rec(2);
+  }
+
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+
+  kfp_status upload_units() {
+    order_units();
+    if (units_dev) cudaFree(units_dev);
+    units_dev = nullptr;
+    KFP_CUDA_TRY(cudaMalloc(&units_dev, sizeof(kfp::BatchUnit) * std::max<size_t>(units.size(), 1)));
+    KFP_CUDA_TRY(cudaMemcpy(units_dev, units.data(), sizeof(kfp::BatchUnit) * units.size(), cudaMemcpyHostToDevice));
+    drop_graph();
+    return KFP_OK;
+  }
+
+  kfp_status sweep(int max_iters, double tol, int tol_kind, int* iters_done) {
+    if (iters_done) *iters_done = 0;
+    if (max_iters < 0 || (tol_kind != 0 && tol_kind != 1))
+      return fail(KFP_EINVAL, "need max_iters >= 0 and tol_kind in {0, 1}");
+    if (max_iters == 0) return KFP_OK;
+    for (kfp_swr* h : inst) {
+      kfp_status rc = h->ensure_history(max_iters);
+      if (rc) return fail(rc, "%s", h->last_error.c_str());
+      KFP_CUDA_TRY(cudaMemsetAsync(h->iter, 0, sizeof(int), stream));
+    }
+    if (!(flags & KFP_FLAG_NO_GRAPH) && !exec) {
+      if (!cap_stream) KFP_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+      KFP_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_iteration(cap_stream, true);
+      cudaGraph_t gr = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cap_stream, &gr);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KFP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      }
+      graph = gr;
+      KFP_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    int done = 0;
+    bool converged = false;
+    kfp_status rc = KFP_OK;
+    for (int it = 0; it < max_iters; ++it) {
+      if (exec) {
+        KFP_CUDA_TRY(cudaGraphLaunch(exec, stream));
+      } else {
+        enqueue_iteration(stream, false);
+        KFP_CUDA_TRY(cudaGetLastError());
+      }
+      ++done;
+      if (flags & KFP_FLAG_PROFILE) {
+        KFP_CUDA_TRY(cudaEventSynchronize(ev[2]));
+        float a = 0, b = 0;
+        KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        t_sweep += a;
+        t_reduce += b;
+      }
+      if (tol > 0) {
+        double worst = 0.0;
+        for (kfp_swr* h : inst) {
+          if (h->g.S < 2) continue;
+          rc = h->read_scalars();
+          if (rc) return fail(rc, "%s", h->last_error.c_str());
+          const double v = tol_kind == 0 ? h->host_scal[1] : h->host_scal[0];
+          if (!std::isfinite(v)) { rc = fail(KFP_ENUMERIC, "non-finite interface norm"); break; }
+          worst = std::max(worst, v);
+        }
+        if (rc) break;
+        if (worst < tol) { converged = true; break; }
+      }
+    }
+    for (kfp_swr* h : inst) {
+      kfp_status r2 = h->pull_history(done);
+      if (r2) return fail(r2, "%s", h->last_error.c_str());
+      h->iterations += done;
+      r2 = h->check_flag();
+      if (r2) return fail(r2, "%s", h->last_error.c_str());
+    }
+    iterations += done;
+    if (iters_done) *iters_done = done;
+    if (rc) return rc;
+    if (tol > 0 && !converged) return fail(KFP_ENOTCONV, "tolerance %g not reached in %d iterations", tol, done);
+    return KFP_OK;
+  }
+
+  void release() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (probs_dev) cudaFree(probs_dev);
+    if (units_dev) cudaFree(units_dev);
+    for (kfp_swr* h : inst) {
+      if (!h) continue;
+      cudaStreamSynchronize(h->stream);
+      h->release();
+      delete h;
+    }
+    inst.clear();
+  }
+};
+
+namespace {
+
+template <typename T>
+kfp_status batch_setup(kfp_batch* b) {
+  std::vector<kfp::BatchProblem<T>> host(b->inst.size());
+  b->units.clear();
+  b->max_nt = 0;
+  b->cells_per_iter = 0;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    kfp_swr* h = b->inst[i];
+    std::memset(&host[i], 0, sizeof host[i]);
+    host[i].maps = h->maps;
+    host[i].args = h->tma_args<T>();
+    host[i].nt = h->g.nt;
+    host[i].fmode = h->fmode;
+    b->max_nt = std::max(b->max_nt, h->g.nt);
+    b->cells_per_iter += h->g.cells_per_iter;
+    const int nbx = (h->g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock;
+    for (int s = 0; s < h->g.S; ++s)
+      for (int bx = 0; bx < nbx; ++bx)
+        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk});
+  }
+  KFP_CUDA_TRY_ON(b, cudaMalloc(&b->probs_dev, sizeof(kfp::BatchProblem<T>) * host.size()));
+  KFP_CUDA_TRY_ON(b, cudaMemcpy(b->probs_dev, host.data(), sizeof(kfp::BatchProblem<T>) * host.size(),
+                          cudaMemcpyHostToDevice));
+  constexpr int NST = kfp_batch::nst<T>();
+  const int sm = (int)kfp_swr::tma_smem_bytes<T>();
+  KFP_CUDA_TRY_ON(b, cudaFuncSetAttribute((const void*)kfp::batch_pass_kernel<T, true, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  KFP_CUDA_TRY_ON(b, cudaFuncSetAttribute((const void*)kfp::batch_pass_kernel<T, false, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  return b->upload_units();
+}
+
+thread_local std::string g_batch_create_error;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 
@@ -1144,6 +1384,106 @@ void kfp_swr_destroy(kfp_swr_t h) {
 }
 
 const char* kfp_swr_last_error(kfp_swr_t h) { return h ? h->last_error.c_str() : ""; }
+
+kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* probs, int count, void* cuda_stream,
+                            kfp_batch_t* out) {
+  g_batch_create_error.clear();
+  if (!out) return KFP_EINVAL;
+  *out = nullptr;
+  if (!descs || !probs || count < 1) {
+    g_batch_create_error = "need descs, probs and count >= 1";
+    return KFP_EINVAL;
+  }
+  kfp_batch* b = new (std::nothrow) kfp_batch();
+  if (!b) return KFP_ENOMEM;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->prec = descs[0].prec;
+  b->flags = descs[0].flags;
+  kfp_status rc = KFP_OK;
+  if (b->prec != KFP_F64 && b->prec != KFP_F32) {
+    g_batch_create_error = "a batch runs in KFP_F64 or KFP_F32";
+    rc = KFP_ENOTSUP;
+  }
+  for (int i = 0; i < count && !rc; ++i) {
+    if (descs[i].prec != b->prec) {
+      g_batch_create_error = "all problems of a batch need the same precision";
+      rc = KFP_EINVAL;
+      break;
+    }
+    kfp_swr_desc d = descs[i];
+    d.flags &= ~(unsigned)(KFP_FLAG_GENERIC | KFP_FLAG_PROFILE);
+    kfp_swr_t h = nullptr;
+    rc = kfp_swr_create(&d, &probs[i], cuda_stream, &h);
+    if (rc) {
+      g_batch_create_error = std::string("problem ") + std::to_string(i) + ": " + kfp_swr_create_error();
+      break;
+    }
+    b->inst.push_back(h);
+    if (!h->use_tma) {
+      g_batch_create_error = "problem " + std::to_string(i) + ": the batched sweep needs at most one forcing term";
+      rc = KFP_ENOTSUP;
+    }
+  }
+  if (!rc) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (auto& e : b->ev)
+      if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = KFP_ECUDA;
+    if (!rc) rc = b->prec == KFP_F64 ? batch_setup<double>(b) : batch_setup<float>(b);
+    if (rc) g_batch_create_error = b->last_error;
+  }
+  if (rc) {
+    b->release();
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return KFP_OK;
+}
+
+kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order) {
+  if (!b) return KFP_EINVAL;
+  if (blocks_per_sm < 0 || blocks_per_sm > 64 || unit_order < 0 || unit_order > 1)
+    return b->fail(KFP_EINVAL, "need 0 <= blocks_per_sm <= 64 and unit_order in {0, 1}");
+  b->blocks_per_sm = blocks_per_sm;
+  b->unit_order = unit_order;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return b->fail(KFP_ECUDA, "sync failed");
+  return b->upload_units();
+}
+
+kfp_status kfp_batch_sweep(kfp_batch_t b, int max_iters, double tol, int tol_kind, int* iters_done) {
+  if (!b) return KFP_EINVAL;
+  b->last_error.clear();
+  return b->sweep(max_iters, tol, tol_kind, iters_done);
+}
+
+kfp_status kfp_batch_instance(kfp_batch_t b, int index, kfp_swr_t* h) {
+  if (!b || !h) return KFP_EINVAL;
+  if (index < 0 || index >= (int)b->inst.size()) return b->fail(KFP_EINVAL, "index out of range");
+  *h = b->inst[index];
+  return KFP_OK;
+}
+
+kfp_status kfp_batch_stats(kfp_batch_t b, long long* iterations, long long* cell_updates_per_iter, double* sweep_ms,
+                           double* reduce_ms) {
+  if (!b) return KFP_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return b->fail(KFP_ECUDA, "sync failed");
+  if (iterations) *iterations = b->iterations;
+  if (cell_updates_per_iter) *cell_updates_per_iter = b->cells_per_iter;
+  if (sweep_ms) *sweep_ms = b->t_sweep;
+  if (reduce_ms) *reduce_ms = b->t_reduce;
+  return KFP_OK;
+}
+
+void kfp_batch_destroy(kfp_batch_t b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  b->release();
+  delete b;
+}
+
+const char* kfp_batch_last_error(kfp_batch_t b) { return b ? b->last_error.c_str() : g_batch_create_error.c_str(); }
 
 const char* kfp_swr_create_error(void) { return g_create_error.c_str(); }
 

@@ -27,7 +27,9 @@ KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC = 1, 2, 4
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
-            "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters")
+            "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters",
+            "kfp_batch_create", "kfp_batch_configure", "kfp_batch_sweep", "kfp_batch_instance", "kfp_batch_stats",
+            "kfp_batch_destroy", "kfp_batch_last_error")
 KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -80,6 +82,19 @@ def load(rebuild: bool = False):
             lib.kfp_swr_stats.argtypes = [vp, llp, llp, ip, _dp, _dp, _dp]
             lib.kfp_swr_counters.argtypes = [vp, llp, llp, _dp]
             lib.kfp_swr_counters.restype = ctypes.c_int
+            lib.kfp_batch_create.argtypes = [ctypes.POINTER(kfp_swr_desc), ctypes.POINTER(kfp_swr_problem), i, vp,
+                                             ctypes.POINTER(vp)]
+            lib.kfp_batch_configure.argtypes = [vp, i, i]
+            lib.kfp_batch_sweep.argtypes = [vp, i, ctypes.c_double, i, ip]
+            lib.kfp_batch_instance.argtypes = [vp, i, ctypes.POINTER(vp)]
+            lib.kfp_batch_stats.argtypes = [vp, llp, llp, _dp, _dp]
+            lib.kfp_batch_destroy.argtypes = [vp]
+            lib.kfp_batch_destroy.restype = None
+            lib.kfp_batch_last_error.argtypes = [vp]
+            lib.kfp_batch_last_error.restype = ctypes.c_char_p
+            for name in ("kfp_batch_create", "kfp_batch_configure", "kfp_batch_sweep", "kfp_batch_instance",
+                         "kfp_batch_stats"):
+                getattr(lib, name).restype = ctypes.c_int
             lib.kfp_swr_destroy.argtypes = [vp]
             lib.kfp_swr_destroy.restype = None
             lib.kfp_swr_last_error.argtypes = [vp]
@@ -200,6 +215,112 @@ def cell_updates_per_iteration(prob) -> int:
     return (prob.nx + 1) * nodes * prob.nt
 
 
+def _marshal(prob, precision: str, flags: int, inputs_on: str, keep: list):
+    """Build (kfp_swr_desc, kfp_swr_problem) for a Problem; buffers are appended to keep."""
+    import torch
+
+    on_dev = inputs_on == "device"
+
+    def put(a):
+        if a is None:
+            return None
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+        t = t.to("cuda") if on_dev else t.pin_memory()
+        keep.append(t)
+        return t.data_ptr()
+
+    S = prob.nstrips
+    p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
+    q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
+    keep.extend([p, q])
+    desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S, prob.overlap,
+                        KFP_ROBIN if prob.robin else KFP_DIRICHLET, p.ctypes.data if p is not None else None,
+                        q.ctypes.data if q is not None else None, PRECISIONS[precision], flags)
+    cdata = kfp_swr_problem(1 if on_dev else 0, put(prob.u0), int(prob.f_time.shape[0]), put(prob.f_time),
+                            put(prob.f_space), put(prob.bc_xin), put(prob.bc_v), put(prob.lam0))
+    return desc, cdata
+
+
+class Batch:
+    """Independent problems swept together (one launch per time step for all)."""
+
+    def __init__(self, probs, precision: str = "f64", stream=None, inputs_on: str = "device", graph: bool = True,
+                 profile: bool = False):
+        import torch
+
+        self.probs = list(probs)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        keep = []
+        flags = (0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
+        pairs = [_marshal(p, precision, flags, inputs_on, keep) for p in self.probs]
+        descs = (kfp_swr_desc * len(pairs))(*[d for d, _ in pairs])
+        cdat = (kfp_swr_problem * len(pairs))(*[c for _, c in pairs])
+        if inputs_on == "device":
+            torch.cuda.current_stream().synchronize()
+        lib = load()
+        out = ctypes.c_void_p()
+        st = lib.kfp_batch_create(descs, cdat, len(pairs), ctypes.c_void_p(int(self.stream.cuda_stream)),
+                                  ctypes.byref(out))
+        if st != KFP_OK:
+            raise KfpError(st, lib.kfp_batch_last_error(None).decode())
+        self.b = out.value
+        self._handles = {}
+
+    def _check(self, st, allow=()):
+        if st != KFP_OK and st not in allow:
+            raise KfpError(st, load().kfp_batch_last_error(self.b).decode())
+        return st
+
+    def configure(self, blocks_per_sm: int = 0, unit_order: int = 0) -> None:
+        self._check(load().kfp_batch_configure(self.b, blocks_per_sm, unit_order))
+
+    def sweep(self, max_iters: int, tol: float = 0.0, tol_kind: int = 0, allow_notconv: bool = True) -> int:
+        done = ctypes.c_int()
+        self._check(load().kfp_batch_sweep(self.b, max_iters, tol, tol_kind, ctypes.byref(done)),
+                    allow=(KFP_ENOTCONV,) if allow_notconv else ())
+        return done.value
+
+    def handle(self, index: int) -> int:
+        if index not in self._handles:
+            h = ctypes.c_void_p()
+            self._check(load().kfp_batch_instance(self.b, index, ctypes.byref(h)))
+            self._handles[index] = h.value
+        return self._handles[index]
+
+    def view(self, index: int) -> "SWR":
+        """An SWR-like read-only view of problem `index` (results only)."""
+        v = SWR.__new__(SWR)
+        v.prob = self.probs[index]
+        v.h = self.handle(index)
+        v._owned = False
+        return v
+
+    def stats(self) -> dict:
+        it, cells = ctypes.c_longlong(), ctypes.c_longlong()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(load().kfp_batch_stats(self.b, ctypes.byref(it), ctypes.byref(cells), ctypes.byref(a),
+                                           ctypes.byref(b)))
+        return {"iterations": it.value, "cell_updates_per_iter": cells.value, "sweep_ms": a.value,
+                "reduce_ms": b.value}
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            load().kfp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class SWR:
     """One problem resident on the current CUDA device.
 
@@ -295,9 +416,9 @@ class SWR:
         return kfp_swr_counters(self.h)
 
     def close(self) -> None:
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             kfp_swr_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -1,0 +1,96 @@
+"""Batched sweep: many uneven problems in one launch per time step.
+
+Every problem of a batch runs exactly the arithmetic of its own handle, so its
+results must be bit-identical to a single-problem run, for every launch shape the
+autotuner can pick, and within the FP64 parity tolerance of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1306_4596_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RD = inputs.random_data
+
+
+def batch_problems():
+    return [
+        inputs.small_robin(),                                                           # time-dependent forcing
+        RD(90, 256, 6, 0.002, 2, 3, False, seed=40, nforce=1, boundary_data=False),     # Dirichlet, overlap 3
+        RD(77, 192, 4, 0.002, 3, 0, True, p=4.0, q=2.0, seed=41, nforce=0, boundary_data=False),  # no forcing
+        RD(150, 300, 7, 0.002, 3, 4, True, p=5.0, seed=42, nforce=1, constant_in_time=True,
+           boundary_data=False),                                                        # pre-scaled forcing
+        RD(37, 24, 3, 0.01, 3, 2, False, seed=43, nforce=1),                            # boundary data
+        inputs.gaussian_bumps(200, 256, 12, 1e-3, 4, p=6.0, seed=44),
+        RD(29, 16, 1, 0.02, 2, 1, True, p=2.0, seed=45, nforce=1),                      # a single step
+    ]
+
+
+def single_results(prob, precision, iters):
+    from paper_1306_4596_gb300 import swr
+    with swr.SWR(prob, precision) as s:
+        s.sweep(iters)
+        return s.solution(), s.traces(), s.error()[3]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_batch_equals_single_problem_runs(precision):
+    from paper_1306_4596_gb300 import swr
+    probs = batch_problems()
+    iters = 3
+    ref = [single_results(p, precision, iters) for p in probs]
+    for bps, order in ((0, 0), (1, 0), (1, 1), (2, 1)):
+        with swr.Batch(probs, precision) as b:
+            b.configure(bps, order)
+            n = b.sweep(iters)
+            assert n == iters
+            for i, p in enumerate(probs):
+                v = b.view(i)
+                u, lam, hist = v.solution(), v.traces(), v.error()[3]
+                assert np.array_equal(u, ref[i][0]), (bps, order, i)
+                assert np.array_equal(lam, ref[i][1]), (bps, order, i)
+                assert np.array_equal(hist, ref[i][2]), (bps, order, i)
+
+
+def test_batch_matches_oracle():
+    from paper_1306_4596_gb300 import swr
+    probs = batch_problems()
+    with swr.Batch(probs, "f64") as b:
+        b.sweep(2)
+        for i, p in enumerate(probs):
+            lam = p.lam0.copy() if p.lam0 is not None else np.zeros(oracle.trace_shape(p))
+            for _ in range(2):
+                lam, bands, u_T = oracle.swr_iteration(p, lam)
+            v = b.view(i)
+            assert np.abs(v.solution() - u_T).max() <= 1e-12 * np.abs(u_T).max()
+            if p.nstrips > 1:
+                assert np.abs(v.traces() - lam).max() <= 1e-12 * np.abs(lam).max()
+
+
+def test_batch_tolerance_and_autotune(tmp_path, monkeypatch):
+    from paper_1306_4596_gb300 import autotune, swr
+    monkeypatch.setenv("KFP_SWR_CACHE", str(tmp_path))
+    probs = [inputs.manufactured(64, 64, 20, 0.1, nstrips=2, overlap=0, robin=True, p=8.0),
+             inputs.gaussian_bumps(96, 128, 30, 2.5e-3, 4, p=6.0, seed=7)]
+    with swr.Batch(probs, "f64") as b:
+        t1 = autotune.tune(b, "f64")
+        assert not t1["cached"] and len(t1["candidates"]) == 4
+        n = b.sweep(300, 1e-12, 1)
+        assert n < 300
+        for i in range(2):
+            assert b.view(i).error()[0] < 1e-12
+    with swr.Batch(probs, "f64") as b:
+        t2 = autotune.tune(b, "f64")
+        assert t2["cached"] and (t2["blocks_per_sm"], t2["unit_order"]) == (t1["blocks_per_sm"], t1["unit_order"])
+
+
+def test_batch_rejects_unsupported():
+    from paper_1306_4596_gb300 import swr
+    with pytest.raises(swr.KfpError) as ei:
+        swr.Batch([inputs.small_robin()], "mixed")
+    assert ei.value.status == swr.KFP_ENOTSUP
+    with pytest.raises(swr.KfpError) as ei:
+        swr.Batch([RD(61, 32, 5, 0.01, 4, 1, True, p=3.0, seed=18, nforce=2)], "f64")
+    assert ei.value.status == swr.KFP_ENOTSUP
