@@ -13,8 +13,9 @@ timed region; the state of one step (3 x 68 MB) is larger than L2 (129 MB).
 Extra keys: "roofline" (sweep kernel: FP64 is bound by the FP64 pipe, FP32 by HBM),
 "cpu_baseline" (the CPU oracle on a bounded sample), "e2e" (through the C ABI from
 pinned host buffers, copies included), "clocks" (nvidia-smi during the timed
-region), "variants" (the FP32 form) and "time_to_tol" (wall time to e_mis < 1e-8 for
-the plain FP64 form and the mixed-precision form).
+region), "variants" (the FP32 form), "time_to_tol" (wall time to e_mis < 1e-8 for
+the plain FP64 form and the mixed-precision form) and "batched" (256 uneven seeded
+problems swept together, FP64 and FP32, autotuned launch shape).
 
 --impl reference times the CPU oracle (the reference arm of this repository) on the
 host cores on a bounded sample of the same workload.
@@ -222,6 +223,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, FP32, time-to-tol and CPU legs")
     ap.add_argument("--cpu-nt", type=int, default=60, help="time steps of the CPU-baseline sample")
     ap.add_argument("--ttol-iters", type=int, default=400, help="FP64 iteration cap of the time-to-1e-8 run")
+    ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched leg (0 = skip it)")
     ap.add_argument("--ref-nt", type=int, default=6, help="time steps per reference-arm step")
     ap.add_argument("--nt", type=int, default=None,
                     help="shorter time window (profiling captures only; the JSON line records it)")
@@ -350,6 +352,35 @@ def main():
         if ttol["f64"]["reached"] and ttol["mixed"]["reached"]:
             ttol["speedup_mixed_vs_f64"] = ttol["f64"]["seconds"] / ttol["mixed"]["seconds"]
         line["time_to_tol"] = {"tol": 1e-8, "norm": "e_mis (FP64 sweep)", **ttol}
+
+        # ---- batched form: uneven problems swept together (autotuned launch shape) -------
+        if args.batch_count > 0:
+            from paper_1306_4596_gb300 import autotune
+            batch_probs = inputs.batch_instances(args.batch_count)
+            bcells = sum(swr_mod.cell_updates_per_iteration(p) for p in batch_probs)
+            batched = {"instances": args.batch_count,
+                       "workload": "seeded instances: Nx~U{128..1024}, Nv=S*U{ceil(256/S)..floor(2048/S)}, "
+                                   "S~U{2,4,8,16}, Robin p log-uniform [0.5,16], Nt~U{200..1000}, v in [-4,4], "
+                                   "CFL 0.8, Gaussian bumps (seeds 3000+i)",
+                       "cell_updates_per_step": bcells}
+            for prec in ("f64", "f32"):
+                with swr_mod.Batch(batch_probs, prec) as bt:
+                    tuned = autotune.tune(bt, prec, use_cache=False)
+                    torch.cuda.synchronize()
+                    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    nsteps = 2
+                    start.record(torch.cuda.current_stream())
+                    bt.sweep(nsteps)
+                    end.record(torch.cuda.current_stream())
+                    end.synchronize()
+                    bms = start.elapsed_time(end)
+                batched[prec] = {"value": bcells * nsteps / (bms / 1e3), "unit": UNIT, "steps": nsteps,
+                                 "ms_per_step": bms / nsteps,
+                                 "launch_shape": {"blocks_per_sm": tuned["blocks_per_sm"],
+                                                  "unit_order": tuned["unit_order"]},
+                                 "candidates_ms": [round(c["ms"], 2) for c in tuned["candidates"]]}
+            del batch_probs
+            line["batched"] = batched
 
         # ---- CPU oracle on a bounded sample -------------------------------------------
         rate, cells, secs = cpu_oracle_rate(prob, args.cpu_nt)
