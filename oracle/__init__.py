@@ -84,6 +84,8 @@ def _load():
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip, _dp, _dp]
             lib.kfo_monolithic.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(_Problem), _dp, _dp]
             lib.kfo_thomas.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.kfo_swr_adjoint.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(_Problem), _dp, ctypes.c_int,
+                                            _dp, _dp, _dp]
             _lib = lib
     return _lib
 
@@ -193,6 +195,21 @@ def monolithic(prob, all_levels: bool = False):
     u_all = np.zeros((prob.nt + 1, prob.nv + 1, prob.nx + 1)) if all_levels else None
     _check(_load().kfo_monolithic(ctypes.byref(m.desc), ctypes.byref(m.prob), _ptr(u_T), _ptr(u_all)))
     return (u_T, u_all) if all_levels else u_T
+
+
+def swr_adjoint(prob, K: int, lam0: Optional[np.ndarray] = None):
+    """Discrete adjoint of K parallel SWR iterations (Robin, no overlap): returns
+    (J, dJ/dp, dJ/dq), J = dt hx sum (u_j - u_{j+1})^2 on the interface nodes of the
+    K-th iterate."""
+    m = _Marshalled(prob)
+    if lam0 is None:
+        lam0 = prob.lam0
+    J = ctypes.c_double()
+    gp = np.zeros(max(prob.nstrips - 1, 1))
+    gq = np.zeros(max(prob.nstrips - 1, 1))
+    _check(_load().kfo_swr_adjoint(ctypes.byref(m.desc), ctypes.byref(m.prob), _ptr(_f64(lam0)), K,
+                                   ctypes.byref(J), _ptr(gp), _ptr(gq)))
+    return J.value, gp[: prob.nstrips - 1], gq[: prob.nstrips - 1]
 
 
 def thomas(a, b, c, d):

@@ -377,3 +377,167 @@ int kfo_monolithic(const kfo_desc* d, const kfo_problem* pb, double* u_T, double
   io.u_all = u_all;
   return solve_strip(&one, pb, 0, &io, u_T);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of K parallel SWR iterations (Robin, no overlap).        */
+/*                                                                          */
+/* Per strip and time step the forward scheme is A u^{n+1} = E u^n + rhs,    */
+/* where A (tridiagonal, per column) holds the Robin coefficient             */
+/* 1 + 2r + 2 p dt/hv on the strip's top row and 1 + 2r + 2 q dt/hv on its   */
+/* bottom row, E is the explicit upwind transport, and the Robin rows carry  */
+/* + (2 dt/hv) lambda_in.  Without overlap the outgoing data are             */
+/* lambda_out = (p + q) u_node - lambda_in (Section 6.3, SWR2 / SWR4).       */
+/* The adjoint solves A^T w^{n+1} = dJ/du^{n+1} + (p + q) lambda_out_bar     */
+/* + E^T w^{n+2} backward in time; lambda_in_bar = (2 dt/hv) w_node -        */
+/* lambda_out_bar; dJ/dp gets -(2 dt/hv) w_node u_node (through A) and       */
+/* lambda_out_bar u_node (through the outgoing data), dJ/dq likewise.        */
+/* The lambda_in_bar of iterate k is the lambda_out_bar of iterate k-1.      */
+/* ------------------------------------------------------------------------ */
+
+/* Row type of node i, column m in strip s (same precedence as solve_strip):
+ * 0 interior, 1 identity (v boundary, x inflow, Dirichlet interface),
+ * 2 Robin top (p + d/dv), 3 Robin bottom (q - d/dv). */
+static int row_kind(const kfo_desc* d, int s, int i, int m) {
+  const double vi = v_node(d, i);
+  if (i == 0 || i == d->nv) return 1;
+  if ((m == 0 && vi > 0) || (m == d->nx && vi < 0)) return 1;
+  if (s < d->nstrips - 1 && i == strip_hi(d, s)) return d->robin ? 2 : 1;
+  if (s > 0 && i == strip_lo(d, s)) return d->robin ? 3 : 1;
+  return 0;
+}
+
+static void row_matrix(const kfo_desc* d, int s, int kind, double* a, double* b, double* c) {
+  const double hv = hv_of(d), r = d->dt / (hv * hv);
+  *a = 0.0; *b = 1.0; *c = 0.0;
+  if (kind == 0) { *a = -r; *b = 1.0 + 2.0 * r; *c = -r; }
+  if (kind == 2) { *a = -2.0 * r; *b = 1.0 + 2.0 * r + 2.0 * d->p[s] * d->dt / hv; }
+  if (kind == 3) { *b = 1.0 + 2.0 * r + 2.0 * d->q[s - 1] * d->dt / hv; *c = -2.0 * r; }
+}
+
+/* Adjoint of strip s over one iterate.  bands: that iterate's interface-node values
+ * [S-1][2][nt][1][nx+1]; lbar_out: adjoint of the data the strip produced (trace
+ * layout); lbar_in (accumulated): adjoint of the data the strip consumed. */
+static int adjoint_strip(const kfo_desc* d, int s, int last, const double* bands, const double* lbar_out,
+                         double* lbar_in, double* gp, double* gq) {
+  const int S = d->nstrips, nx = d->nx, nxp = d->nx + 1, nt = d->nt;
+  const int lo = strip_lo(d, s), hi = strip_hi(d, s), L = hi - lo + 1;
+  const double hv = hv_of(d), dthx = d->dt * hx_of(d), two_dt_hv = 2.0 * d->dt / hv;
+  const int has_top = s < S - 1, has_bot = s > 0;
+  const size_t tr = (size_t)nt * nxp;  /* one trace / one band (overlap 0) array */
+  double* w_next = (double*)calloc((size_t)L * nxp, sizeof(double));
+  double* w_cur = (double*)calloc((size_t)L * nxp, sizeof(double));
+  double* a = (double*)malloc(sizeof(double) * (size_t)L);
+  double* b = (double*)malloc(sizeof(double) * (size_t)L);
+  double* c = (double*)malloc(sizeof(double) * (size_t)L);
+  double* at = (double*)malloc(sizeof(double) * (size_t)L);
+  double* ct = (double*)malloc(sizeof(double) * (size_t)L);
+  double* mu = (double*)malloc(sizeof(double) * (size_t)L);
+  double* x = (double*)malloc(sizeof(double) * (size_t)L);
+  if (!w_next || !w_cur || !a || !b || !c || !at || !ct || !mu || !x) {
+    free(w_next); free(w_cur); free(a); free(b); free(c); free(at); free(ct); free(mu); free(x);
+    return KFO_ENOMEM;
+  }
+  for (int n = nt - 1; n >= 0; --n) { /* time level n+1 */
+    const int have_next = (n + 1 < nt);
+    for (int m = 0; m <= nx; ++m) {
+      for (int l = 0; l < L; ++l) {
+        const int i = lo + l;
+        double e = 0.0; /* (E^T w^{n+2})_{i,m} */
+        if (have_next) {
+          const double vi = v_node(d, i);
+          const double cabs = fabs(vi * d->dt / hx_of(d));
+          if (row_kind(d, s, i, m) != 1) e += (1.0 - cabs) * w_next[(size_t)l * nxp + m];
+          if (vi > 0 && m + 1 <= nx && row_kind(d, s, i, m + 1) != 1) e += cabs * w_next[(size_t)l * nxp + m + 1];
+          if (vi < 0 && m - 1 >= 0 && row_kind(d, s, i, m - 1) != 1) e += cabs * w_next[(size_t)l * nxp + m - 1];
+        }
+        mu[l] = e;
+        int k = row_kind(d, s, i, m);
+        row_matrix(d, s, k, &a[l], &b[l], &c[l]);
+      }
+      if (has_top) {
+        const double uh = bands[(((size_t)s * 2 + 0) * tr) + (size_t)n * nxp + m];
+        const double uo = bands[(((size_t)s * 2 + 1) * tr) + (size_t)n * nxp + m];
+        if (last) mu[L - 1] += 2.0 * dthx * (uh - uo);
+        mu[L - 1] += (d->p[s] + d->q[s]) * lbar_out[(((size_t)s * 2 + 1) * tr) + (size_t)n * nxp + m];
+      }
+      if (has_bot) {
+        const double ul = bands[((((size_t)s - 1) * 2 + 1) * tr) + (size_t)n * nxp + m];
+        const double uo = bands[((((size_t)s - 1) * 2 + 0) * tr) + (size_t)n * nxp + m];
+        if (last) mu[0] += -2.0 * dthx * (uo - ul);
+        mu[0] += (d->p[s - 1] + d->q[s - 1]) * lbar_out[((((size_t)s - 1) * 2 + 0) * tr) + (size_t)n * nxp + m];
+      }
+      /* transposed system: sub-diagonal c_{l-1}, super-diagonal a_{l+1} */
+      for (int l = 0; l < L; ++l) {
+        at[l] = l > 0 ? c[l - 1] : 0.0;
+        ct[l] = l < L - 1 ? a[l + 1] : 0.0;
+      }
+      int rc = kfo_thomas(L, at, b, ct, mu, x);
+      if (rc) {
+        free(w_next); free(w_cur); free(a); free(b); free(c); free(at); free(ct); free(mu); free(x);
+        return rc;
+      }
+      for (int l = 0; l < L; ++l) w_cur[(size_t)l * nxp + m] = x[l];
+      if (has_top) {
+        const int k = row_kind(d, s, hi, m);
+        const double uh = bands[(((size_t)s * 2 + 0) * tr) + (size_t)n * nxp + m];
+        const double lo_bar = lbar_out[(((size_t)s * 2 + 1) * tr) + (size_t)n * nxp + m];
+        const double wr = (k == 2) ? x[L - 1] : 0.0;
+        lbar_in[(((size_t)s * 2 + 0) * tr) + (size_t)n * nxp + m] += two_dt_hv * wr - lo_bar;
+        gp[s] += -two_dt_hv * wr * uh + lo_bar * uh;
+        gq[s] += lo_bar * uh;
+      }
+      if (has_bot) {
+        const int k = row_kind(d, s, lo, m);
+        const double ul = bands[((((size_t)s - 1) * 2 + 1) * tr) + (size_t)n * nxp + m];
+        const double lo_bar = lbar_out[((((size_t)s - 1) * 2 + 0) * tr) + (size_t)n * nxp + m];
+        const double wr = (k == 3) ? x[0] : 0.0;
+        lbar_in[((((size_t)s - 1) * 2 + 1) * tr) + (size_t)n * nxp + m] += two_dt_hv * wr - lo_bar;
+        gq[s - 1] += -two_dt_hv * wr * ul + lo_bar * ul;
+        gp[s - 1] += lo_bar * ul;
+      }
+    }
+    double* t = w_next;
+    w_next = w_cur;
+    w_cur = t;
+  }
+  free(w_next); free(w_cur); free(a); free(b); free(c); free(at); free(ct); free(mu); free(x);
+  return KFO_OK;
+}
+
+int kfo_swr_adjoint(const kfo_desc* d, const kfo_problem* pb, const double* lam0, int K, double* J,
+                    double* grad_p, double* grad_q) {
+  int rc = kfo_validate(d);
+  if (rc) return rc;
+  if (!d->robin || d->overlap != 0 || d->nstrips < 2 || K < 1) return KFO_EINVAL;
+  const int S = d->nstrips, nxp = d->nx + 1, nt = d->nt;
+  const size_t ntr = (size_t)(S - 1) * 2 * nt * nxp; /* traces = bands (overlap 0) */
+  double* lam = (double*)calloc(ntr, sizeof(double));
+  double* lam_new = (double*)calloc(ntr, sizeof(double));
+  double* bands = (double*)calloc(ntr * (size_t)K, sizeof(double));
+  double* lbar_out = (double*)calloc(ntr, sizeof(double));
+  double* lbar_in = (double*)calloc(ntr, sizeof(double));
+  if (!lam || !lam_new || !bands || !lbar_out || !lbar_in) {
+    free(lam); free(lam_new); free(bands); free(lbar_out); free(lbar_in);
+    return KFO_ENOMEM;
+  }
+  if (lam0) memcpy(lam, lam0, sizeof(double) * ntr);
+  for (int k = 0; k < K && rc == KFO_OK; ++k) {
+    rc = kfo_swr_iteration(d, pb, lam, lam_new, bands + (size_t)k * ntr, NULL);
+    double* t = lam; lam = lam_new; lam_new = t;
+  }
+  if (rc == KFO_OK) {
+    double jl2 = 0.0;
+    kfo_interface_norms(d, bands + (size_t)(K - 1) * ntr, NULL, NULL, NULL, NULL, &jl2);
+    if (J) *J = jl2;
+    for (int j = 0; j < S - 1; ++j) { grad_p[j] = 0.0; grad_q[j] = 0.0; }
+    for (int k = K; k >= 1 && rc == KFO_OK; --k) {
+      memset(lbar_in, 0, sizeof(double) * ntr);
+      for (int s = 0; s < S && rc == KFO_OK; ++s)
+        rc = adjoint_strip(d, s, k == K, bands + (size_t)(k - 1) * ntr, lbar_out, lbar_in, grad_p, grad_q);
+      /* the data iterate k consumed were produced by iterate k-1 in the same slots */
+      double* t = lbar_out; lbar_out = lbar_in; lbar_in = t;
+    }
+  }
+  free(lam); free(lam_new); free(bands); free(lbar_out); free(lbar_in);
+  return rc;
+}

@@ -96,6 +96,19 @@ int kfo_swr_solve(const kfo_desc* d, const kfo_problem* pb, double* lam, int max
  * u_all (may be NULL) receives every time level, [nt+1][nv+1][nx+1]. */
 int kfo_monolithic(const kfo_desc* d, const kfo_problem* pb, double* u_T, double* u_all);
 
+/*
+ * Discrete adjoint (gradient) of K parallel SWR iterations with Robin transmission
+ * and no overlap.  Objective: J = dt hx sum_j sum_{n=1..nt} sum_m (u_j - u_{j+1})^2,
+ * the squared L2 mismatch on the interface nodes of the K-th iterate (u_j is the
+ * lower strip of interface j).  lam0 (may be NULL = 0) is lambda^0.  Outputs J and
+ * dJ/dp_j, dJ/dq_j for j = 0..S-2 (grad_p, grad_q of length S-1).  The forward run
+ * keeps the interface-node values of every iterate; the adjoint solves the
+ * transposed implicit-Euler systems backward in time and the transposed exchange
+ * backward over the iterations.  Returns KFO_EINVAL unless robin and overlap == 0.
+ */
+int kfo_swr_adjoint(const kfo_desc* d, const kfo_problem* pb, const double* lam0, int K, double* J,
+                    double* grad_p, double* grad_q);
+
 /* Plain Thomas algorithm for a tridiagonal system of size n (exported for the
  * oracle's own unit tests): a = sub-diagonal (a[0] unused), b = diagonal,
  * c = super-diagonal (c[n-1] unused), d = right-hand side, x = solution. */

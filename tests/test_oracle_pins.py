@@ -432,3 +432,46 @@ def test_maximum_principle_nonnegative_data():
     prob = inputs.gaussian_bumps(32, 64, 40, 2e-3, nstrips=4, p=4.0, seed=9)
     res = oracle.swr_solve(prob, 3, 0.0, 0)
     assert res["u_T"].min() > -1e-15
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of K SWR iterations (gradient of the interface L2 mismatch)
+# ---------------------------------------------------------------------------
+
+def _j_after(prob, K, p, q):
+    pr = prob.replace()
+    pr.p, pr.q = np.array(p, float), np.array(q, float)
+    lam = np.zeros(oracle.trace_shape(prob)) if prob.lam0 is None else prob.lam0.copy()
+    for _ in range(K):
+        lam, bands, _ = oracle.swr_iteration(pr, lam)
+    return oracle.interface_norms(pr, bands)[2]
+
+
+@pytest.mark.parametrize("case", [
+    lambda: inputs.random_data(6, 12, 4, 0.05, 3, 0, True, p=[2.0, 3.0], q=[1.5, 2.5], seed=3, nforce=1),
+    lambda: inputs.random_data(9, 16, 5, 0.04, 4, 0, True, p=[1.0, 4.0, 2.0], seed=4, nforce=2),
+    lambda: inputs.gaussian_bumps(12, 32, 6, 5e-3, 4, p=[3.0, 5.0, 2.0], seed=5),
+], ids=["random_3_strips_pq", "random_4_strips_2_terms", "bumps_4_strips"])
+def test_adjoint_matches_central_differences(case):
+    prob = case()
+    K = 3
+    J, gp, gq = oracle.swr_adjoint(prob, K)
+    assert abs(J - _j_after(prob, K, prob.p, prob.q)) <= 1e-14 * max(J, 1e-300)
+    h = 1e-6
+    for j in range(prob.nstrips - 1):
+        for grad, which in ((gp, "p"), (gq, "q")):
+            pp, qq = prob.p.copy(), prob.q.copy()
+            arr = pp if which == "p" else qq
+            arr[j] += h
+            jp = _j_after(prob, K, pp, qq)
+            arr[j] -= 2 * h
+            jm = _j_after(prob, K, pp, qq)
+            fd = (jp - jm) / (2 * h)
+            assert abs(grad[j] - fd) <= 1e-6 * max(abs(fd), 1e-3 * J), (which, j, grad[j], fd)
+
+
+def test_adjoint_rejects_unsupported():
+    with pytest.raises(oracle.OracleError):
+        oracle.swr_adjoint(inputs.small_dirichlet(), 2)
+    with pytest.raises(oracle.OracleError):
+        oracle.swr_adjoint(inputs.random_data(6, 12, 4, 0.05, 3, 2, True, seed=3, nforce=1), 2)
