@@ -161,6 +161,25 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
                          int* launches_per_iter, double* sweep_ms, double* exchange_ms,
                          double* error_ms);
 
+/*
+ * Gradient of the interface mismatch after K iterations with respect to the Robin
+ * parameters (discrete adjoint; Robin transmission, no overlap, KFP_F64).
+ *   J = dt hx sum_j sum_{n=1..nt} sum_m (u_j - u_{j+1})^2 on the interface nodes of
+ *   the K-th iterate from lambda^0 = lam0 (NULL = 0; host or device memory), i.e. the
+ *   j_l2 norm of kfp_swr_sweep.  grad_p, grad_q (host, [S-1], may be NULL) receive
+ *   dJ/dp_j and dJ/dq_j (for one-sided OSWR(p) with q = p, dJ/dp_j + dJ/dq_j).
+ * The forward part runs K iterations on the handle (they count in its history and
+ * leave lambda^K as its interface data); the adjoint solves the transposed
+ * implicit-Euler systems backward in time and the transposed exchange backward over
+ * the iterates, using only the interface-node values of every iterate.  Errors:
+ * KFP_ENOTSUP (other transmission, overlap, precision), KFP_EINVAL, KFP_ECUDA. */
+kfp_status kfp_swr_gradient(kfp_swr_t h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
+                            double* grad_q);
+
+/* Replace the Robin parameters (host arrays [S-1]; q = NULL means q = p) and rebuild
+ * the factors in place; the interface data are kept.  Errors: KFP_EINVAL. */
+kfp_status kfp_swr_set_robin(kfp_swr_t h, const double* p, const double* q);
+
 /* Largest interface count accepted by kfp_iface_norms_noalloc. */
 #define KFP_NOALLOC_MAX_INTERFACES 64
 

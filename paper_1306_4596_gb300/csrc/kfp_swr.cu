@@ -10,6 +10,7 @@
 #include "../../include/kfp_swr.h"
 #include "kfp_kernels.cuh"
 #include "kfp_sweep_tma.cuh"
+#include "kfp_adjoint.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -244,6 +245,18 @@ struct kfp_swr {
   long long inner_iterations = 0;
   int inner_max = 4000;
   double inner_rtol = 1e-7;
+  // kept for kfp_swr_set_robin: the constant-in-time forcing (FMODE 1) and its factor
+  std::vector<double> Fh_keep;
+  double a0_keep = 0.0;
+  // adjoint buffers (allocated by the first kfp_swr_gradient)
+  double* adj_bands = nullptr;   // [K][S-1][2][nt][nx+1]
+  double* adj_lbar = nullptr;    // [2][S-1][2][nt][nx+1]
+  double* adj_contrib = nullptr; // [S-1][4][nt][nx+1]
+  double* adj_w = nullptr;       // [2][rows][nx+1]
+  double* adj_scratch = nullptr; // [rows][nx+1]
+  double* adj_fac = nullptr;     // [S][3][3][Lmax]
+  double* adj_grad = nullptr;    // [S-1][2]
+  int adj_K = 0;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double t_sweep = 0, t_exchange = 0, t_error = 0;
@@ -617,7 +630,8 @@ struct kfp_swr {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
-                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage, d_res};
+                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage, d_res,
+                    adj_bands, adj_lbar, adj_contrib, adj_w, adj_scratch, adj_fac, adj_grad};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (host_scal) cudaFreeHost(host_scal);
@@ -799,6 +813,8 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
   std::vector<T> rec, gf;
   kfp_status rc = build_records<T>(h, coef, Fh, a0, &rec, h->fmode == 1 ? &gf : nullptr);
   if (rc) return rc;
+  h->Fh_keep = Fh;
+  h->a0_keep = a0;
   rc = alloc(h, &h->rec, sizeof(T) * rec.size());
   if (rc) return rc;
   KFP_CUDA_TRY_H(cudaMemcpy(h->rec, rec.data(), sizeof(T) * rec.size(), cudaMemcpyHostToDevice));
@@ -998,6 +1014,178 @@ kfp_status create_inner(kfp_swr* h, const kfp_swr_desc* d) {
   }
   in->d_ext = h->d_res;
   h->inner = in;
+  return KFP_OK;
+}
+
+// Transposed implicit-Euler factors for the adjoint: per strip and column class,
+// ascending elimination of A^T (sub-diagonal c_{r-1}, super-diagonal a_{r+1}).
+std::vector<double> build_adjoint_factors(const Geometry& g) {
+  std::vector<double> fac((size_t)g.S * 3 * 3 * g.Lmax, 0.0);
+  std::vector<double> a(g.Lmax), b(g.Lmax), c(g.Lmax), cpv(g.Lmax);
+  const double r = g.r;
+  for (int s = 0; s < g.S; ++s) {
+    const kfp::StripInfo& st = g.strips[s];
+    const int L = st.L;
+    for (int cls = 0; cls < 3; ++cls) {
+      for (int l = 0; l < L; ++l) {
+        const int i = st.lo + l;
+        const double vi = g.v0 + i * g.hv;
+        const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
+        const bool top = st.has_top && i == st.hi, bot = st.has_bot && i == st.lo;
+        a[l] = 0.0; b[l] = 1.0; c[l] = 0.0;
+        if (i == 0 || i == g.nv || inflow) continue;
+        if (top) { a[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.p_top * g.dt / g.hv; continue; }
+        if (bot) { c[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.q_bot * g.dt / g.hv; continue; }
+        a[l] = -r; b[l] = 1 + 2 * r; c[l] = -r;
+      }
+      double* f = &fac[((size_t)s * 3 + cls) * 3 * g.Lmax];
+      for (int l = 0; l < L; ++l) {
+        const double sub = l > 0 ? c[l - 1] : 0.0, sup = l < L - 1 ? a[l + 1] : 0.0;
+        const double piv = b[l] - (l > 0 ? sub * cpv[l - 1] : 0.0);
+        const double gi = 1.0 / piv;
+        cpv[l] = sup * gi;
+        f[0 * g.Lmax + l] = gi;
+        f[1 * g.Lmax + l] = sub;
+        f[2 * g.Lmax + l] = cpv[l];
+      }
+    }
+  }
+  return fac;
+}
+
+kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
+                         double* grad_q) {
+  Geometry& g = h->g;
+  if (!g.robin || g.ov != 0 || g.S < 2 || h->prec != KFP_F64 || h->inner)
+    return h->fail(KFP_ENOTSUP, "the adjoint needs FP64, Robin transmission, no overlap and >= 2 strips");
+  if (K < 1) return h->fail(KFP_EINVAL, "need K >= 1");
+  const size_t nxp = g.nx + 1, per = (size_t)g.nt * nxp, ntr = h->n_trace;
+  const size_t field = (size_t)g.rows * nxp;
+  kfp_status rc;
+  if (!h->adj_lbar) {
+    if ((rc = alloc(h, (void**)&h->adj_lbar, sizeof(double) * 2 * ntr))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_contrib, sizeof(double) * (size_t)(g.S - 1) * 4 * per))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_w, sizeof(double) * 2 * field))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_scratch, sizeof(double) * field))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_fac, sizeof(double) * (size_t)g.S * 9 * g.Lmax))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_grad, sizeof(double) * 2 * (g.S - 1)))) return rc;
+  }
+  if (K > h->adj_K) {
+    if (h->adj_bands) cudaFree(h->adj_bands);
+    h->adj_bands = nullptr;
+    if ((rc = alloc(h, (void**)&h->adj_bands, sizeof(double) * (size_t)K * ntr))) return rc;
+    h->adj_K = K;
+  }
+  std::vector<double> fac = build_adjoint_factors(g);
+  KFP_CUDA_TRY_H(cudaMemcpy(h->adj_fac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice));
+  // forward: K iterations from lambda^0, keeping every iterate's interface-node values
+  if (lam0) {
+    KFP_CUDA_TRY_H(cudaMemcpyAsync(h->lam_in, lam0, sizeof(double) * ntr,
+                                   lam0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  } else {
+    KFP_CUDA_TRY_H(cudaMemsetAsync(h->lam_in, 0, sizeof(double) * ntr, h->stream));
+  }
+  if ((rc = h->ensure_history(K))) return rc;
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream));
+  for (int k = 0; k < K; ++k) {
+    if ((rc = h->launch_iteration(kfp_swr::kStandard))) return rc;
+    KFP_CUDA_TRY_H(cudaMemcpyAsync(h->adj_bands + (size_t)k * ntr, h->bands, sizeof(double) * ntr,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if ((rc = h->pull_history(K))) return rc;
+  h->iterations += K;
+  if ((rc = h->check_flag())) return rc;
+  if (J) *J = h->history[h->history.size() - 1];
+  // adjoint, backward over iterates and time levels
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_lbar, 0, sizeof(double) * 2 * ntr, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_contrib, 0, sizeof(double) * (size_t)(g.S - 1) * 4 * per, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_w, 0, sizeof(double) * 2 * field, h->stream));
+  kfp::AdjArgs A;
+  A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.S = g.S; A.Lmax = g.Lmax;
+  A.two_dt_hv = 2.0 * g.dt / g.hv;
+  A.dthx = g.dt * g.hx;
+  A.strips = h->strips;
+  A.fac = h->adj_fac;
+  A.cabs = (const double*)h->cabs;
+  A.sgn = h->sgn;
+  A.contrib = h->adj_contrib;
+  A.w0 = h->adj_w;
+  A.w1 = h->adj_w + field;
+  A.scratch = h->adj_scratch;
+  A.rows = g.rows;
+  double* lb_out = h->adj_lbar;
+  double* lb_in = h->adj_lbar + ntr;
+  const dim3 grid((unsigned)((nxp + 127) / 128), g.S);
+  for (int k = K; k >= 1; --k) {
+    A.bands = h->adj_bands + (size_t)(k - 1) * ntr;
+    A.lbar_out = lb_out;
+    A.lbar_in = lb_in;
+    for (int l = g.nt; l >= 1; --l) kfp::adjoint_level_kernel<<<grid, 128, 0, h->stream>>>(A, l, k == K ? 1 : 0);
+    std::swap(lb_out, lb_in);
+  }
+  kfp::gradient_reduce_kernel<<<2 * (g.S - 1), kfp::kReduceThreads, 0, h->stream>>>(h->adj_contrib, per,
+                                                                                     h->adj_grad);
+  KFP_CUDA_TRY_H(cudaGetLastError());
+  std::vector<double> gr(2 * (g.S - 1));
+  KFP_CUDA_TRY_H(cudaMemcpyAsync(gr.data(), h->adj_grad, sizeof(double) * gr.size(), cudaMemcpyDeviceToHost,
+                                 h->stream));
+  KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < g.S - 1; ++j) {
+    if (grad_p) grad_p[j] = gr[2 * j];
+    if (grad_q) grad_q[j] = gr[2 * j + 1];
+  }
+  return KFP_OK;
+}
+
+// New Robin parameters: strip table, LU factors, coefficient records and the
+// pre-scaled forcing are rebuilt in place (same sizes, so captured graphs stay valid).
+template <typename T>
+kfp_status refresh_tables(kfp_swr* h) {
+  Geometry& g = h->g;
+  KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
+  KFP_CUDA_TRY_H(cudaMemcpy(h->strips, g.strips.data(), sizeof(kfp::StripInfo) * g.S, cudaMemcpyHostToDevice));
+  std::vector<double> coef = build_factors(g);
+  if (h->prec == KFP_F64) {
+    KFP_CUDA_TRY_H(cudaMemcpy(h->coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> c32(coef.begin(), coef.end());
+    KFP_CUDA_TRY_H(cudaMemcpy(h->coef, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice));
+  }
+  if (h->use_tma) {
+    std::vector<T> rec, gf;
+    kfp_status rc = build_records<T>(h, coef, h->Fh_keep, h->a0_keep, &rec, h->fmode == 1 ? &gf : nullptr);
+    if (rc) return rc;
+    KFP_CUDA_TRY_H(cudaMemcpy(h->rec, rec.data(), sizeof(T) * rec.size(), cudaMemcpyHostToDevice));
+    if (h->fmode == 1)
+      KFP_CUDA_TRY_H(cudaMemcpy(h->GF, gf.data(), sizeof(T) * gf.size(), cudaMemcpyHostToDevice));
+  }
+  return KFP_OK;
+}
+
+kfp_status set_robin_impl(kfp_swr* h, const double* p, const double* q) {
+  Geometry& g = h->g;
+  if (!g.robin || g.S < 2) return h->fail(KFP_EINVAL, "no Robin interfaces");
+  if (!p) return h->fail(KFP_EINVAL, "p is NULL");
+  for (int j = 0; j < g.S - 1; ++j) {
+    const double pj = p[j], qj = q ? q[j] : p[j];
+    if (!(pj > 0) || !(qj > 0) || !std::isfinite(pj) || !std::isfinite(qj))
+      return h->fail(KFP_EINVAL, "Robin parameters must be finite and > 0");
+  }
+  for (int j = 0; j < g.S - 1; ++j) {
+    g.p[j] = p[j];
+    g.q[j] = q ? q[j] : p[j];
+  }
+  for (int s = 0; s < g.S; ++s) {
+    kfp::StripInfo& st = g.strips[s];
+    if (s < g.S - 1) { st.p_top = g.p[s]; st.q_top = g.q[s]; }
+    if (s > 0) { st.p_bot = g.p[s - 1]; st.q_bot = g.q[s - 1]; }
+  }
+  kfp_status rc = h->prec == KFP_F64 ? refresh_tables<double>(h) : refresh_tables<float>(h);
+  if (rc) return rc;
+  if (h->inner) {
+    rc = set_robin_impl(h->inner, p, q);
+    if (rc) return h->fail(rc, "inner solver: %s", h->inner->last_error.c_str());
+  }
   return KFP_OK;
 }
 
@@ -1363,6 +1551,19 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
   if (exchange_ms) *exchange_ms = h->t_exchange;
   if (error_ms) *error_ms = h->t_error;
   return KFP_OK;
+}
+
+kfp_status kfp_swr_gradient(kfp_swr_t h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
+                            double* grad_q) {
+  if (!h) return KFP_EINVAL;
+  h->last_error.clear();
+  return gradient_impl(h, K, lam0, lam0_on_device, J, grad_p, grad_q);
+}
+
+kfp_status kfp_swr_set_robin(kfp_swr_t h, const double* p, const double* q) {
+  if (!h) return KFP_EINVAL;
+  h->last_error.clear();
+  return set_robin_impl(h, p, q);
 }
 
 kfp_status kfp_swr_counters(kfp_swr_t h, long long* fp64_iterations, long long* fp32_iterations,

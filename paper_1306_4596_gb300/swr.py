@@ -29,7 +29,7 @@ EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_tr
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
             "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters",
             "kfp_batch_create", "kfp_batch_configure", "kfp_batch_sweep", "kfp_batch_instance", "kfp_batch_stats",
-            "kfp_batch_destroy", "kfp_batch_last_error")
+            "kfp_batch_destroy", "kfp_batch_last_error", "kfp_swr_gradient", "kfp_swr_set_robin")
 KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -80,6 +80,10 @@ def load(rebuild: bool = False):
             lib.kfp_swr_bands.argtypes = [vp, i, i, vp, i]
             lib.kfp_swr_solution.argtypes = [vp, vp, i]
             lib.kfp_swr_stats.argtypes = [vp, llp, llp, ip, _dp, _dp, _dp]
+            lib.kfp_swr_gradient.argtypes = [vp, i, vp, i, _dp, _dp, _dp]
+            lib.kfp_swr_gradient.restype = ctypes.c_int
+            lib.kfp_swr_set_robin.argtypes = [vp, vp, vp]
+            lib.kfp_swr_set_robin.restype = ctypes.c_int
             lib.kfp_swr_counters.argtypes = [vp, llp, llp, _dp]
             lib.kfp_swr_counters.restype = ctypes.c_int
             lib.kfp_batch_create.argtypes = [ctypes.POINTER(kfp_swr_desc), ctypes.POINTER(kfp_swr_problem), i, vp,
@@ -175,6 +179,22 @@ def kfp_swr_counters(h: int) -> dict:
     t = ctypes.c_double()
     _check(h, load().kfp_swr_counters(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)))
     return {"fp64_iterations": a.value, "fp32_iterations": b.value, "fp32_sweep_ms": t.value}
+
+
+def kfp_swr_gradient(h: int, K: int, lam0_ptr=None, lam0_on_device: int = 0, nif: int = 1):
+    """(J, dJ/dp, dJ/dq) after K iterations from lambda^0 (discrete adjoint)."""
+    J = ctypes.c_double()
+    gp = np.zeros(max(nif, 1))
+    gq = np.zeros(max(nif, 1))
+    _check(h, load().kfp_swr_gradient(h, K, lam0_ptr, lam0_on_device, ctypes.byref(J), gp.ctypes.data_as(_dp),
+                                      gq.ctypes.data_as(_dp)))
+    return J.value, gp[:nif], gq[:nif]
+
+
+def kfp_swr_set_robin(h: int, p, q=None) -> None:
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    q = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+    _check(h, load().kfp_swr_set_robin(h, p.ctypes.data, None if q is None else q.ctypes.data))
 
 
 def kfp_swr_destroy(h: int) -> None:
@@ -414,6 +434,18 @@ class SWR:
 
     def counters(self) -> dict:
         return kfp_swr_counters(self.h)
+
+    def gradient(self, K: int, lam0: Optional[np.ndarray] = None):
+        """(J, dJ/dp, dJ/dq): J = dt hx sum (u_j - u_{j+1})^2 on the interface nodes after
+        K iterations from lam0 (None = 0)."""
+        lam = None if lam0 is None else np.ascontiguousarray(lam0, dtype=np.float64)
+        return kfp_swr_gradient(self.h, K, None if lam is None else lam.ctypes.data, 0, self.prob.nstrips - 1)
+
+    def set_robin(self, p, q=None) -> None:
+        kfp_swr_set_robin(self.h, p, q)
+        self.prob = self.prob.replace()
+        self.prob.p = np.array(p, dtype=np.float64)
+        self.prob.q = np.array(p if q is None else q, dtype=np.float64)
 
     def close(self) -> None:
         if getattr(self, "h", None) and getattr(self, "_owned", True):
