@@ -15,7 +15,9 @@ Extra keys: "roofline" (sweep kernel: FP64 is bound by the FP64 pipe, FP32 by HB
 pinned host buffers, copies included), "clocks" (nvidia-smi during the timed
 region), "variants" (the FP32 form), "time_to_tol" (wall time to e_mis < 1e-8 for
 the plain FP64 form and the mixed-precision form) and "batched" (256 uneven seeded
-problems swept together, FP64 and FP32, autotuned launch shape).
+problems swept together, FP64 and FP32, autotuned launch shape) and "adjoint" (time of
+one gradient of the interface mismatch after 10 iterations, and 20 Adam steps on the
+Robin parameters).
 
 --impl reference times the CPU oracle (the reference arm of this repository) on the
 host cores on a bounded sample of the same workload.
@@ -224,6 +226,7 @@ def main():
     ap.add_argument("--cpu-nt", type=int, default=60, help="time steps of the CPU-baseline sample")
     ap.add_argument("--ttol-iters", type=int, default=400, help="FP64 iteration cap of the time-to-1e-8 run")
     ap.add_argument("--batch-count", type=int, default=256, help="problems in the batched leg (0 = skip it)")
+    ap.add_argument("--adjoint-steps", type=int, default=20, help="Adam steps of the adjoint leg (0 = skip it)")
     ap.add_argument("--ref-nt", type=int, default=6, help="time steps per reference-arm step")
     ap.add_argument("--nt", type=int, default=None,
                     help="shorter time window (profiling captures only; the JSON line records it)")
@@ -381,6 +384,30 @@ def main():
                                  "candidates_ms": [round(c["ms"], 2) for c in tuned["candidates"]]}
             del batch_probs
             line["batched"] = batched
+
+        # ---- adjoint: dJ/dp after K = 10 iterations, and Adam on log p ----------------
+        if args.adjoint_steps > 0:
+            from paper_1306_4596_gb300 import adjoint as adj
+            aprob = inputs.adjoint_workload()
+            K = 10
+            acells = swr_mod.cell_updates_per_iteration(aprob) * K
+            with swr_mod.SWR(aprob, "f64") as s:
+                s.gradient(K)  # warm-up (allocations, graph capture)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                J0, gp0, gq0 = s.gradient(K)
+                torch.cuda.synchronize()
+                tgrad = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                res = adj.optimize_robin(s, K, steps=args.adjoint_steps, lr=0.1)
+                topt = time.perf_counter() - t0
+            line["adjoint"] = {
+                "workload": "Nx=512, Nv=1024, 8 Robin strips (7 interface parameters, p = 4), dt=4e-4, Nt=500, "
+                            "Gaussian bumps (seed 5); J = dt hx sum (u_j - u_{j+1})^2 after K = 10 iterations",
+                "gradient_seconds": tgrad, "forward_cell_updates": acells, "J": J0,
+                "dJ_dp_one_sided": (gp0 + gq0).tolist(),
+                "adam": {"steps": args.adjoint_steps, "lr": 0.1, "seconds": topt, "J_start": res["history"][0]["J"],
+                         "J_end": res["J"], "p_end": [round(float(v), 4) for v in res["p"]]}}
 
         # ---- CPU oracle on a bounded sample -------------------------------------------
         rate, cells, secs = cpu_oracle_rate(prob, args.cpu_nt)

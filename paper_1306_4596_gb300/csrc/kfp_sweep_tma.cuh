@@ -298,12 +298,16 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
   T xx[kChunk], hn[kChunk];
   T* pout = nullptr;
   auto drain = [&]() {
+    T y_last = T(0);
 #pragma unroll
     for (int t = 0; t < kChunk; ++t) {
+      if (t > 0 && out_lane) *pout = y_last;
+      if (t > 0) pout += step;
       y_prev = fma(hn[t], y_prev, xx[t]);
-      if (out_lane) *pout = y_prev;
-      pout += step;
+      y_last = y_prev;
     }
+    if (out_lane) *pout = y_last;
+    pout += step;
     pend = false;
   };
   for (int c = 0; c < NC; ++c) {
@@ -333,7 +337,8 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
       // (A) back-substitution chain of this chunk, interleaved with the deferred
       //     elimination chain of the previous chunk
       T uu[kChunk];
-      if (pend) {
+      constexpr bool kLateStore = sizeof(T) == 4;  // measured: helps FP32, not FP64
+      if (pend && !kLateStore) {
 #pragma unroll
         for (int t = 0; t < kChunk; ++t) {
           const int r = UP ? t : (kChunk - 1 - t);
@@ -344,6 +349,23 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
           if (out_lane) *pout = y_prev;
           pout += step;
         }
+        pend = false;
+      } else if (pend) {
+        // each y is stored one row late, so that no store waits on the FMA just issued
+        T y_last = T(0);
+#pragma unroll
+        for (int t = 0; t < kChunk; ++t) {
+          const int r = UP ? t : (kChunk - 1 - t);
+          const T tile = sm.tile[q][r][cbase];
+          if (MODE == 0) uu[t] = tile;
+          else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
+          if (t > 0 && out_lane) *pout = y_last;
+          if (t > 0) pout += step;
+          y_prev = fma(hn[t], y_prev, xx[t]);
+          y_last = y_prev;
+        }
+        if (out_lane) *pout = y_last;
+        pout += step;
         pend = false;
       } else {
 #pragma unroll
@@ -366,14 +388,20 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
           outT += step;
         }
       } else {
-        // (B) shuffles and the terms that do not depend on the previous row
+        // (B) shuffles (all issued before their first use) and the terms that do not
+        //     depend on the previous row
+        T nb[kChunk];
+        if (kLateStore) {
+#pragma unroll
+          for (int t = 0; t < kChunk; ++t) nb[t] = shfl_val(uu[t], src);
+        }
 #pragma unroll
         for (int t = 0; t < kChunk; ++t) {
           const int r = UP ? t : (kChunk - 1 - t);
           const T* rc = &sm.rec[q][r][cls * 8];
           T ncp_unused, ca, cb, chn;
           load_coef4(rc, ncp_unused, ca, cb, chn);
-          const T unb = shfl_val(uu[t], src);
+          const T unb = kLateStore ? nb[t] : shfl_val(uu[t], src);
           T gterm;
           if (FMODE == 0) gterm = T(0);
           else if (FMODE == 1) gterm = sm.frc[q][r][cbase];
