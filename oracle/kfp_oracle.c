@@ -280,7 +280,12 @@ int kfo_swr_iteration(const kfo_desc* d, const kfo_problem* pb, const double* la
     strip_io io;
     memset(&io, 0, sizeof io);
     if (s > 0) {
-      io.lam_bot = lam_in ? lam_in + ((size_t)(s - 1) * 2 + 1) * tr : NULL;
+      /* serial form (SWR3 uses lambda_2^k just produced by the strip below) or the
+       * parallel form of the Remark (lambda_2^{k-1}) */
+      if (d->gauss_seidel && lam_out)
+        io.lam_bot = lam_out + ((size_t)(s - 1) * 2 + 1) * tr;
+      else
+        io.lam_bot = lam_in ? lam_in + ((size_t)(s - 1) * 2 + 1) * tr : NULL;
       io.out_bot = lam_out ? lam_out + ((size_t)(s - 1) * 2 + 0) * tr : NULL;
       io.band_bot = bands ? bands + ((size_t)(s - 1) * 2 + 1) * bd : NULL;
     }

@@ -42,6 +42,9 @@ typedef struct {
   int robin;           /* 0: classical (Dirichlet) transmission, 1: optimized (Robin) */
   const double* p;     /* [S-1] Robin p_j of interface j (lower strip's top, p + d/dv) */
   const double* q;     /* [S-1] Robin q_j of interface j (upper strip's bottom, q - d/dv) */
+  int gauss_seidel;    /* 0: parallel form (every strip uses iterate k-1, Remark of Section
+                          6.3); 1: serial form SWR1-SWR4 -- strips in increasing order, each
+                          taking lambda_2 from the strip below of the same iteration */
 } kfo_desc;
 
 typedef struct {

@@ -51,6 +51,7 @@ class Problem:
     bc_v: Optional[np.ndarray] = None
     lam0: Optional[np.ndarray] = None
     name: str = ""
+    gauss_seidel: bool = False  # serial SWR1-SWR4 order instead of the parallel form
 
     @property
     def hx(self) -> float:

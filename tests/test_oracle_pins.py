@@ -475,3 +475,37 @@ def test_adjoint_rejects_unsupported():
         oracle.swr_adjoint(inputs.small_dirichlet(), 2)
     with pytest.raises(oracle.OracleError):
         oracle.swr_adjoint(inputs.random_data(6, 12, 4, 0.05, 3, 2, True, seed=3, nforce=1), 2)
+
+
+# ---------------------------------------------------------------------------
+# Serial (Gauss-Seidel) order SWR1-SWR4 of Section 6.3
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("robin,overlap", [(False, 2), (True, 0), (True, 2)])
+def test_gauss_seidel_two_strips_is_the_squared_parallel_map(robin, overlap):
+    """Two subdomains: with lambda = (lambda_1, lambda_2), the parallel map is
+    [[0, A], [B, 0]] and the serial map SWR1-SWR4 is [[A B, 0], [B, 0]] -- it ignores
+    lambda_2 of the previous iterate, its lambda_2 <- lambda_1 block is B and its
+    lambda_1 <- lambda_1 block is that of the squared parallel map.  (Spectral radii
+    are not compared directly: the maps are block-triangular in time, so their
+    eigenvalues are highly defective and numerically ill-conditioned.)"""
+    prob = inputs.random_data(6, 16, 4, 0.04, 2, overlap, robin, p=4.0, seed=5)
+    MJ, _ = _trace_map(prob)
+    MG, _ = _trace_map(prob.replace(gauss_seidel=True))
+    n = MJ.shape[0] // 2  # first half lambda_1, second half lambda_2
+    scale = np.abs(MJ).max()
+    assert np.abs(MG[:, n:]).max() == 0.0
+    assert np.abs(MG[n:, :n] - MJ[n:, :n]).max() <= 1e-13 * scale
+    MJ2 = MJ @ MJ
+    assert np.abs(MG[:n, :n] - MJ2[:n, :n]).max() <= 1e-12 * max(np.abs(MJ2).max(), 1e-300)
+    assert np.abs(MJ[:n, :n]).max() == 0.0 and np.abs(MJ[n:, n:]).max() == 0.0
+
+
+@pytest.mark.parametrize("robin,overlap", [(False, 3), (True, 0)])
+def test_gauss_seidel_fixed_point_and_speed(robin, overlap):
+    prob = inputs.manufactured(64, 64, 20, 0.1, nstrips=4, overlap=overlap, robin=robin, p=8.0)
+    mono = oracle.monolithic(prob)
+    jac = oracle.swr_solve(prob, 400, 1e-13, 0)
+    gs = oracle.swr_solve(prob.replace(gauss_seidel=True), 400, 1e-13, 0)
+    np.testing.assert_allclose(gs["u_T"], mono, rtol=0, atol=1e-11)
+    assert gs["iters"] < jac["iters"], (gs["iters"], jac["iters"])
