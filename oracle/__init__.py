@@ -45,7 +45,8 @@ class _Desc(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("nx", ctypes.c_int), ("nv", ctypes.c_int), ("nt", ctypes.c_int),
         ("nstrips", ctypes.c_int), ("overlap", ctypes.c_int), ("robin", ctypes.c_int),
-        ("p", _dp), ("q", _dp), ("gauss_seidel", ctypes.c_int),
+        ("p", _dp), ("q", _dp), ("gauss_seidel", ctypes.c_int), ("neumann_v", ctypes.c_int),
+        ("periodic_x", ctypes.c_int),
     ]
 
 
@@ -120,7 +121,8 @@ class _Marshalled:
         self.desc = _Desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt,
                           S, prob.overlap if overlap is None else overlap,
                           int(prob.robin if robin is None else robin), _ptr(self.p), _ptr(self.q),
-                          int(getattr(prob, "gauss_seidel", False)))
+                          int(getattr(prob, "gauss_seidel", False)), int(getattr(prob, "neumann_v", False)),
+                          int(getattr(prob, "periodic_x", False)))
         self.prob = _Problem(_ptr(self.u0), int(self.f_time.shape[0]), _ptr(self.f_time),
                              _ptr(self.f_space), _ptr(self.bc_xin), _ptr(self.bc_v))
 

@@ -58,6 +58,7 @@ int kfo_validate(const kfo_desc* d) {
   if (d->nx < 1 || d->nv < 2 || d->nt < 1 || d->nstrips < 1) return KFO_EINVAL;
   if (!(d->x1 > d->x0) || !(d->v1 > d->v0) || !(d->dt > 0)) return KFO_EINVAL;
   if (d->nv % d->nstrips != 0) return KFO_EINVAL;
+  if (d->periodic_x && d->nx < 2) return KFO_EINVAL;
   if (d->nstrips > 1) {
     int w = cells_per_strip(d);
     if (w < 2 || d->overlap < 0 || d->overlap >= w) return KFO_EINVAL;
@@ -128,11 +129,14 @@ static double explicit_part(const kfo_desc* d, const kfo_problem* pb, const doub
   const double* row = un + (size_t)(i - lo) * nxp;
   const double vi = v_node(d, i);
   const double cfl = vi * d->dt / hx_of(d);
+  /* upwind neighbours; periodic x wraps the unknowns m = 0..nx-1 */
+  const int mm = d->periodic_x ? (m - 1 + d->nx) % d->nx : m - 1;
+  const int mp = d->periodic_x ? (m + 1) % d->nx : m + 1;
   double T;
   if (vi > 0)
-    T = row[m] - cfl * (row[m] - row[m - 1]);
+    T = row[m] - cfl * (row[m] - row[mm]);
   else if (vi < 0)
-    T = row[m] - cfl * (row[m + 1] - row[m]);
+    T = row[m] - cfl * (row[mp] - row[m]);
   else
     T = row[m];
   double f = 0.0;
@@ -164,22 +168,33 @@ static int solve_strip(const kfo_desc* d, const kfo_problem* pb, int s, const st
   }
   for (int l = 0; l < L; ++l)
     memcpy(un + (size_t)l * nxp, pb->u0 + (size_t)(lo + l) * nxp, sizeof(double) * nxp);
-  if (io->u_all) memcpy(io->u_all, un, sizeof(double) * (size_t)L * nxp);
 
+  if (d->periodic_x) /* node nx repeats node 0 */
+    for (int l = 0; l < L; ++l) un[(size_t)l * nxp + nx] = un[(size_t)l * nxp + 0];
+  if (io->u_all) memcpy(io->u_all, un, sizeof(double) * (size_t)L * nxp);
+  const int mlast = d->periodic_x ? nx - 1 : nx;
   for (int n = 0; n < nt; ++n) {
-    for (int m = 0; m <= nx; ++m) {
+    for (int m = 0; m <= mlast; ++m) {
       for (int l = 0; l < L; ++l) {
         const int i = lo + l;
         const double vi = v_node(d, i);
         a[l] = 0.0; b[l] = 1.0; c[l] = 0.0;
-        if (i == 0) { /* v boundary at v0 */
+        if (i == 0 && !d->neumann_v) { /* v boundary at v0 */
           R[l] = pb->bc_v ? pb->bc_v[((size_t)(n + 1) * 2 + 0) * nxp + m] : 0.0;
-        } else if (i == d->nv) { /* v boundary at v1 */
+        } else if (i == d->nv && !d->neumann_v) { /* v boundary at v1 */
           R[l] = pb->bc_v ? pb->bc_v[((size_t)(n + 1) * 2 + 1) * nxp + m] : 0.0;
-        } else if (m == 0 && vi > 0) { /* inflow at x0 */
+        } else if (!d->periodic_x && m == 0 && vi > 0) { /* inflow at x0 */
           R[l] = pb->bc_xin ? pb->bc_xin[((size_t)(n + 1) * 2 + 0) * (d->nv + 1) + i] : 0.0;
-        } else if (m == nx && vi < 0) { /* inflow at x1 */
+        } else if (!d->periodic_x && m == nx && vi < 0) { /* inflow at x1 */
           R[l] = pb->bc_xin ? pb->bc_xin[((size_t)(n + 1) * 2 + 1) * (d->nv + 1) + i] : 0.0;
+        } else if (i == 0) { /* zero-flux half cell at v0 */
+          b[l] = 1.0 + 2.0 * r;
+          c[l] = -2.0 * r;
+          R[l] = explicit_part(d, pb, un, lo, i, m, n);
+        } else if (i == d->nv) { /* zero-flux half cell at v1 */
+          a[l] = -2.0 * r;
+          b[l] = 1.0 + 2.0 * r;
+          R[l] = explicit_part(d, pb, un, lo, i, m, n);
         } else if (has_top && i == hi) { /* Q_1 u_s = lambda_1 at beta_s */
           const double lam = io->lam_top ? io->lam_top[(size_t)n * nxp + m] : 0.0;
           if (d->robin) {
@@ -212,9 +227,13 @@ static int solve_strip(const kfo_desc* d, const kfo_problem* pb, int s, const st
       }
       for (int l = 0; l < L; ++l) unew[(size_t)l * nxp + m] = x[l];
     }
+    if (d->periodic_x)
+      for (int l = 0; l < L; ++l) unew[(size_t)l * nxp + nx] = unew[(size_t)l * nxp + 0];
 
-    /* SWR2 / SWR4: interface variables of the new iterate at t^{n+1}. */
+    /* SWR2 / SWR4: interface variables of the new iterate at t^{n+1}.  With periodic x
+       the incoming data of column nx is never used: column nx repeats column 0. */
     for (int m = 0; m <= nx; ++m) {
+      const int mi = (d->periodic_x && m == nx) ? 0 : m;
 #define U(i) unew[(size_t)((i) - lo) * nxp + m]
       if (has_top && io->out_top) { /* lambda_2 of interface s = Q_2 u_s at alpha_s */
         const int al = alpha_node(d, s);
@@ -225,7 +244,7 @@ static int solve_strip(const kfo_desc* d, const kfo_problem* pb, int s, const st
           lam = d->q[s] * U(al) - (U(al + 1) - U(al - 1)) / (2.0 * hv);
         else
           lam = (d->p[s] + d->q[s]) * U(al) -
-                (io->lam_top ? io->lam_top[(size_t)n * nxp + m] : 0.0);
+                (io->lam_top ? io->lam_top[(size_t)n * nxp + mi] : 0.0);
         io->out_top[(size_t)n * nxp + m] = lam;
       }
       if (has_bot && io->out_bot) { /* lambda_1 of interface s-1 = Q_1 u_s at beta_{s-1} */
@@ -237,7 +256,7 @@ static int solve_strip(const kfo_desc* d, const kfo_problem* pb, int s, const st
           lam = d->p[s - 1] * U(be) + (U(be + 1) - U(be - 1)) / (2.0 * hv);
         else
           lam = (d->p[s - 1] + d->q[s - 1]) * U(be) -
-                (io->lam_bot ? io->lam_bot[(size_t)n * nxp + m] : 0.0);
+                (io->lam_bot ? io->lam_bot[(size_t)n * nxp + mi] : 0.0);
         io->out_bot[(size_t)n * nxp + m] = lam;
       }
       for (int k = 0; k <= ov; ++k) {
@@ -323,7 +342,7 @@ int kfo_interface_norms(const kfo_desc* d, const double* bands, const double* la
     for (size_t e = 0; e < bd; ++e) {
       const double diff = lower[e] - upper[e];
       if (fabs(diff) > mis) mis = fabs(diff);
-      sq += diff * diff;
+      if (!(d->periodic_x && (int)(e % nxp) == d->nx)) sq += diff * diff; /* node nx repeats node 0 */
     }
   }
   if (lam_new && lam_old)
@@ -513,7 +532,9 @@ int kfo_swr_adjoint(const kfo_desc* d, const kfo_problem* pb, const double* lam0
                     double* grad_p, double* grad_q) {
   int rc = kfo_validate(d);
   if (rc) return rc;
-  if (!d->robin || d->overlap != 0 || d->nstrips < 2 || K < 1) return KFO_EINVAL;
+  if (!d->robin || d->overlap != 0 || d->nstrips < 2 || K < 1 || d->gauss_seidel || d->neumann_v ||
+      d->periodic_x)
+    return KFO_EINVAL;
   const int S = d->nstrips, nxp = d->nx + 1, nt = d->nt;
   const size_t ntr = (size_t)(S - 1) * 2 * nt * nxp; /* traces = bands (overlap 0) */
   double* lam = (double*)calloc(ntr, sizeof(double));

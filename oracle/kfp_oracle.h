@@ -19,8 +19,10 @@
  *   transport   explicit first-order upwind by the sign of v_i, at t^n.
  *   diffusion   implicit Euler, centred second difference in v:
  *               (1+2r) u_i - r u_{i-1} - r u_{i+1} = T_i + dt f_i, r = dt/hv^2.
- *   x boundary  inflow Dirichlet data (m = 0 where v_i > 0, m = nx where v_i < 0).
- *   v boundary  Dirichlet data at v0 and v1.
+ *   x boundary  inflow Dirichlet data (m = 0 where v_i > 0, m = nx where v_i < 0),
+ *               or periodic (periodic_x).
+ *   v boundary  Dirichlet data at v0 and v1, or homogeneous Neumann half-cell rows
+ *               (1+2r) u_0 - 2r u_1 = R_0 and (1+2r) u_nv - 2r u_{nv-1} = R_nv (neumann_v).
  *   Robin rows  half-cell finite-volume rows for (p + d/dv) u = lambda_1 at the
  *               lower strip's top node and (q - d/dv) u = lambda_2 at the upper
  *               strip's bottom node.
@@ -45,6 +47,10 @@ typedef struct {
   int gauss_seidel;    /* 0: parallel form (every strip uses iterate k-1, Remark of Section
                           6.3); 1: serial form SWR1-SWR4 -- strips in increasing order, each
                           taking lambda_2 from the strip below of the same iteration */
+  int neumann_v;       /* 1: homogeneous Neumann rows at v0 and v1 (the model problem of
+                          Section 6.1) instead of Dirichlet data; bc_v is ignored */
+  int periodic_x;      /* 1: x periodic (Section 6.1): nodes m = 0..nx-1 are the unknowns,
+                          node nx repeats node 0; bc_xin is ignored */
 } kfo_desc;
 
 typedef struct {

@@ -52,6 +52,8 @@ class Problem:
     lam0: Optional[np.ndarray] = None
     name: str = ""
     gauss_seidel: bool = False  # serial SWR1-SWR4 order instead of the parallel form
+    neumann_v: bool = False     # homogeneous Neumann at v0, v1 (Section 6.1) instead of Dirichlet data
+    periodic_x: bool = False    # periodic in x (Section 6.1): node nx repeats node 0
 
     @property
     def hx(self) -> float:

@@ -426,6 +426,13 @@ def test_interface_norms_by_hand():
     e_mis, e_chg, j = oracle.interface_norms(prob, bands, lam_new, lam_old)
     assert e_mis == 0.75 and e_chg == 0.3
     assert abs(j - 0.1 * 0.5 * (0.75 ** 2 + 0.1 ** 2)) < 1e-16
+    # periodic x: column nx (= 2 here) repeats column 0 and is left out of the L2 sum,
+    # so the mismatches -0.75 and 0.2 placed there count only in the maximum
+    per = prob.replace(periodic_x=True)
+    bands[0, 1, 0, 0, 2] = 0.2
+    e_mis, _, j = oracle.interface_norms(per, bands, lam_new, lam_old)
+    assert e_mis == 0.75
+    assert abs(j - 0.1 * 0.5 * 0.1 ** 2) < 1e-18
 
 
 def test_maximum_principle_nonnegative_data():
@@ -509,3 +516,164 @@ def test_gauss_seidel_fixed_point_and_speed(robin, overlap):
     gs = oracle.swr_solve(prob.replace(gauss_seidel=True), 400, 1e-13, 0)
     np.testing.assert_allclose(gs["u_T"], mono, rtol=0, atol=1e-11)
     assert gs["iters"] < jac["iters"], (gs["iters"], jac["iters"])
+
+
+# ---------------------------------------------------------------------------
+# Model-problem boundary conditions of Section 6.1: periodic in x, zero flux in v
+# ---------------------------------------------------------------------------
+
+def _dense_variants(prob):
+    """Dense space-time assembly with homogeneous Neumann rows in v and/or the periodic
+    wrap in x, written from the equations of the scheme (independent of the oracle)."""
+    nx, nv, nt = prob.nx, prob.nv, prob.nt
+    N = (nv + 1) * (nx + 1)
+    idx = lambda i, m: i * (nx + 1) + m
+    hx, hv, dt = prob.hx, prob.hv, prob.dt
+    r = dt / hv ** 2
+    v = prob.v_nodes()
+    per, neu = prob.periodic_x, prob.neumann_v
+    bc_xin = np.zeros((nt + 1, 2, nv + 1)) if prob.bc_xin is None else prob.bc_xin
+    bc_v = np.zeros((nt + 1, 2, nx + 1)) if prob.bc_v is None else prob.bc_v
+    u0 = prob.u0.copy()
+    if per:
+        u0[:, nx] = u0[:, 0]
+    big = np.zeros((nt * N, nt * N))
+    rhs = np.zeros(nt * N)
+    wrap = (lambda m: m % nx) if per else (lambda m: m)
+    for n in range(nt):
+        off = n * N
+        for i in range(nv + 1):
+            for m in range(nx + 1):
+                row = off + idx(i, m)
+                big[row, off + idx(i, m)] = 1.0
+                if per and m == nx:  # duplicate of node 0
+                    big[row, off + idx(i, 0)] = -1.0
+                    continue
+                ident = None
+                if not neu and i == 0:
+                    ident = bc_v[n + 1, 0, m]
+                elif not neu and i == nv:
+                    ident = bc_v[n + 1, 1, m]
+                elif not per and m == 0 and v[i] > 0:
+                    ident = bc_xin[n + 1, 0, i]
+                elif not per and m == nx and v[i] < 0:
+                    ident = bc_xin[n + 1, 1, i]
+                if ident is not None:
+                    rhs[row] = ident
+                    continue
+                big[row, off + idx(i, m)] = 1 + 2 * r
+                if i == 0:  # zero flux: ghost node u_{-1} = u_1
+                    big[row, off + idx(1, m)] = -2 * r
+                elif i == nv:
+                    big[row, off + idx(nv - 1, m)] = -2 * r
+                else:
+                    big[row, off + idx(i - 1, m)] = -r
+                    big[row, off + idx(i + 1, m)] = -r
+                c = v[i] * dt / hx
+                if v[i] > 0:
+                    coeffs = {(i, m): 1 - c, (i, wrap(m - 1)): c}
+                elif v[i] < 0:
+                    coeffs = {(i, m): 1 + c, (i, wrap(m + 1)): -c}
+                else:
+                    coeffs = {(i, m): 1.0}
+                f = sum(prob.f_time[k, n + 1] * prob.f_space[k, i, m] for k in range(prob.f_time.shape[0]))
+                rhs[row] = dt * f
+                for (ii, mm), w in coeffs.items():
+                    if n == 0:
+                        rhs[row] += w * u0[ii, mm]
+                    else:
+                        big[row, (n - 1) * N + idx(ii, mm)] -= w
+    sol = np.linalg.solve(big, rhs)
+    return sol.reshape(nt, nv + 1, nx + 1)
+
+
+VARIANTS = [(True, False), (False, True), (True, True)]
+
+
+@pytest.mark.parametrize("neumann,periodic", VARIANTS)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_dense_spacetime_variants(neumann, periodic, seed):
+    prob = inputs.random_data(5, 8, 3, 0.05, 1, 0, False, seed=seed, v_range=(-1.0, 1.25)).replace(
+        neumann_v=neumann, periodic_x=periodic)
+    dense = _dense_variants(prob)
+    _, u_all = oracle.monolithic(prob, all_levels=True)
+    np.testing.assert_allclose(u_all[1:], dense, rtol=0, atol=1e-13)
+
+
+def _mass(prob, u):
+    """Trapezoid weights in v (half weights on the zero-flux half cells), the periodic
+    unknowns m = 0..nx-1 in x."""
+    w = np.full(prob.nv + 1, prob.hv)
+    w[0] = w[-1] = 0.5 * prob.hv
+    return float(w @ u[:, : prob.nx].sum(axis=1)) * prob.hx
+
+
+@pytest.mark.parametrize("robin,overlap,nstrips", [(True, 0, 1), (True, 0, 4), (False, 3, 4), (True, 2, 2)])
+def test_model_problem_conserves_mass(robin, overlap, nstrips):
+    """Zero-flux v boundaries plus periodic x conserve the discrete mass; a forcing adds
+    dt * its mass per step (exactly, for the converged iterate and the single domain)."""
+    prob = inputs.random_data(24, 32, 12, 0.004, nstrips, overlap, robin, p=3.0, seed=11,
+                              v_range=(-2.0, 2.0)).replace(neumann_v=True, periodic_x=True)
+    _, u_all = oracle.monolithic(prob, all_levels=True)
+    mass = np.array([_mass(prob, u) for u in u_all])
+    src = np.array([sum(prob.f_time[k, n] * _mass(prob, prob.f_space[k]) for k in range(prob.f_time.shape[0]))
+                    for n in range(prob.nt + 1)])
+    np.testing.assert_allclose(np.diff(mass), prob.dt * src[1:], rtol=0, atol=1e-13)
+    if nstrips > 1:
+        res = oracle.swr_solve(prob, 500, 1e-13, 0)
+        assert res["iters"] < 500
+        np.testing.assert_allclose(_mass(prob, res["u_T"]), mass[-1], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(res["u_T"], u_all[-1], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [0, 2, 5])
+@pytest.mark.parametrize("nstrips,robin,overlap", [(1, False, 0), (4, True, 0), (4, False, 2)])
+def test_model_problem_cosine_eigen_solution(k, nstrips, robin, overlap):
+    """cos(k pi i / nv), constant in x, is an exact eigenvector of the zero-flux implicit
+    Euler step with factor 1 / (1 + 4 r sin^2(k pi / (2 nv))); periodic transport leaves
+    x-constant data unchanged."""
+    nx, nv, nt, dt = 6, 32, 10, 0.004
+    hv = 2.0 / nv
+    r = dt / hv ** 2
+    phi = np.cos(k * math.pi * np.arange(nv + 1) / nv)
+    rho = 1.0 / (1.0 + 4.0 * r * math.sin(k * math.pi / (2 * nv)) ** 2)
+    u0 = np.repeat(phi[:, None], nx + 1, axis=1)
+    nif = max(nstrips - 1, 0)
+    prob = inputs.Problem(0, 1, -1.0, 1.0, dt, nx, nv, nt, nstrips, overlap, robin, np.full(nif, 5.0),
+                          np.full(nif, 5.0), u0, np.zeros((1, nt + 1)), np.zeros((1, nv + 1, nx + 1)), None,
+                          None, neumann_v=True, periodic_x=True)
+    exact = rho ** nt * u0
+    if nstrips == 1:
+        np.testing.assert_allclose(oracle.monolithic(prob), exact, rtol=0, atol=2e-14)
+    else:
+        res = oracle.swr_solve(prob, 400, 1e-15, 0)
+        np.testing.assert_allclose(res["u_T"], exact, rtol=0, atol=1e-13)
+
+
+def test_periodic_shift_equivariance():
+    """Rolling every x-dependent input by s columns rolls the solution by s."""
+    prob = inputs.random_data(10, 16, 6, 0.01, 2, 0, True, p=3.0, seed=4, v_range=(-1.5, 1.5)).replace(
+        neumann_v=True, periodic_x=True)
+    s, nx = 3, prob.nx
+
+    def roll(a):
+        a = a.copy()
+        a[..., :nx] = np.roll(a[..., :nx], s, axis=-1)
+        a[..., nx] = a[..., 0]
+        return a
+
+    moved = prob.replace(u0=roll(prob.u0), f_space=roll(prob.f_space), lam0=roll(prob.lam0))
+    a = oracle.swr_solve(prob, 5)
+    b = oracle.swr_solve(moved, 5)
+    np.testing.assert_allclose(b["u_T"], roll(a["u_T"]), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(b["lam"], roll(a["lam"]), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("robin,overlap", [(True, 0), (False, 2)])
+def test_model_problem_trace_map_fixed_point(robin, overlap):
+    prob = inputs.random_data(4, 8, 3, 0.05, 2, overlap, robin, p=3.0, q=5.0, seed=3).replace(
+        neumann_v=True, periodic_x=True)
+    M, c = _trace_map(prob)
+    lam_star = np.linalg.solve(np.eye(len(c)) - M, c).reshape(oracle.trace_shape(prob))
+    _, _, u_T = oracle.swr_iteration(prob, lam_star)
+    np.testing.assert_allclose(u_T, _dense_variants(prob)[-1], rtol=0, atol=1e-12)
