@@ -369,6 +369,8 @@ int kfo_swr_solve(const kfo_desc* d, const kfo_problem* pb, double* lam, int max
     free(lam_new); free(bands);
     return KFO_ENOMEM;
   }
+  if (d->periodic_x) /* periodic x: column nx of the interface data repeats column 0 */
+    for (size_t line = 0; line < ntr / nxp; ++line) lam[line * nxp + d->nx] = lam[line * nxp];
   int k = 0;
   while (k < max_iters) {
     rc = kfo_swr_iteration(d, pb, lam, lam_new, bands, u_T);

@@ -97,6 +97,7 @@ int kfo_interface_norms(const kfo_desc* d, const double* bands, const double* la
  * max_iters iterations ran.  lam holds lambda^0 on entry and the last iterate
  * on exit.  hist (may be NULL) receives max_iters rows of (e_mis, e_chg, j_l2).
  * *iters receives the number of iterations run.  u_T as above (last iterate).
+ * With periodic_x, column nx of lam is set to column 0 on entry (node nx repeats node 0).
  */
 int kfo_swr_solve(const kfo_desc* d, const kfo_problem* pb, double* lam, int max_iters,
                   double tol, int tol_kind, int* iters, double* hist, double* u_T);
