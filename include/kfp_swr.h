@@ -72,6 +72,16 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
 #define KFP_FLAG_NO_GRAPH 1u  /* launch every kernel directly instead of replaying a CUDA graph */
 #define KFP_FLAG_PROFILE 2u   /* time the sweep, exchange and error kernels with CUDA events */
 #define KFP_FLAG_GENERIC 4u   /* use the plain sweep kernel even where the TMA-fed one applies */
+#define KFP_FLAG_GAUSS_SEIDEL 8u /* serial form SWR1-SWR4 of Section 6.3: strips in increasing order,
+                                  * each taking its lower interface data from the strip below in the
+                                  * same iteration (default: the parallel form of the Remark) */
+/* Boundary conditions of the model problem of Section 6.1 (default: Dirichlet data). */
+#define KFP_FLAG_NEUMANN_V 16u   /* zero flux at v0 and v1: half-cell rows (1+2r) u_0 - 2r u_1 = R_0 and
+                                  * (1+2r) u_nv - 2r u_{nv-1} = R_nv; bc_v is ignored */
+#define KFP_FLAG_PERIODIC_X 32u  /* periodic in x: the unknowns are m = 0..nx-1 and node nx repeats
+                                  * node 0 in every output; bc_xin, column nx of u0 and f_space, and
+                                  * column nx of lambda0 / set_traces data are ignored (replaced by
+                                  * column 0); needs nx >= 2 */
 
 typedef struct {
   double x0, x1, v0, v1; /* box [x0,x1] x [v0,v1], x1 > x0, v1 > v0 */

@@ -48,6 +48,7 @@ struct StripInfo {
 template <typename T>
 struct PassArgs {
   int nx, nv, nt, S, ov, P, W, Lmax, nforce, robin;
+  int neumann_v, periodic_x;   // model-problem boundary conditions (Section 6.1)
   double two_dt_hv;            // 2 dt / hv (Robin row)
   double inv_2hv;              // 1 / (2 hv) (centred difference of the Robin trace)
   const StripInfo* strips;     // [S]
@@ -60,6 +61,9 @@ struct PassArgs {
   const double* bc_xin;        // [nt+1][2][nv+1] or nullptr
   const double* bc_v;          // [nt+1][2][nx+1] or nullptr
   const double* lam_in;        // [S-1][2][nt][nx+1] interface data of the previous iterate
+  const double* lam_bot_src;   // where a strip reads its lower interface data: lam_in (parallel
+                               // form) or lam_next (serial form: the strip below, this iterate)
+  int strip0;                  // strip of blockIdx.y = 0 (the serial form launches one strip at a time)
   double* lam_next;            // same shape, written by the sweep
   double* bands;               // [S-1][2][nt][ov+1][nx+1]
   T* Y0;                       // [rows][P] elimination residue, even steps
@@ -83,7 +87,7 @@ sweep_pass_kernel(const PassArgs<T> A, const int k) {
   const int lane = threadIdx.x & 31;
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (w >= A.W) return;  // whole warp leaves together
-  const int s = blockIdx.y;
+  const int s = blockIdx.y + A.strip0;
   const StripInfo st = A.strips[s];
   const int m = w * kOutCols - 1 + lane;
   const int col = m + 1;
@@ -151,7 +155,7 @@ sweep_pass_kernel(const PassArgs<T> A, const int k) {
             lam = st.p_bot * (double)u_m1 + d * A.inv_2hv;
           } else {
             lam = (st.p_bot + st.q_bot) * (double)u -
-                  A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
+                  A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
           }
           A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
         }
@@ -168,9 +172,9 @@ sweep_pass_kernel(const PassArgs<T> A, const int k) {
     const int sg = A.sgn[i];
     const T unb = shfl_val(u, lane - sg);  // upwind neighbour of the same row
     T R;
-    if (i == 0 || i == A.nv) {
+    if (!A.neumann_v && (i == 0 || i == A.nv)) {
       R = (A.bc_v && in_dom) ? (T)A.bc_v[((size_t)k1 * 2 + (i == 0 ? 0 : 1)) * nxp + m] : T(0);
-    } else if ((inflow_side == 0 && sg > 0) || (inflow_side == 1 && sg < 0)) {
+    } else if (!A.periodic_x && ((inflow_side == 0 && sg > 0) || (inflow_side == 1 && sg < 0))) {
       R = A.bc_xin ? (T)A.bc_xin[((size_t)k1 * 2 + inflow_side) * (A.nv + 1) + i] : T(0);
     } else {
       R = u - A.cabs[i] * (u - unb);
@@ -180,7 +184,7 @@ sweep_pass_kernel(const PassArgs<T> A, const int k) {
         const double lam = in_dom ? A.lam_in[(((size_t)s * 2 + 0) * nt + k) * nxp + m] : 0.0;
         R = A.robin ? (T)((double)R + A.two_dt_hv * lam) : (T)lam;
       } else if (l == 0 && st.has_bot) {
-        const double lam = in_dom ? A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + k) * nxp + m] : 0.0;
+        const double lam = in_dom ? A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + k) * nxp + m] : 0.0;
         R = A.robin ? (T)((double)R + A.two_dt_hv * lam) : (T)lam;
       }
     }
@@ -320,7 +324,9 @@ __global__ void correct_kernel(double* __restrict__ lam_in, const double* __rest
 __global__ void __launch_bounds__(kReduceThreads)
 error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double dthx,
              double* partial, unsigned* ticket, double* scal, double* hist, int* iter,
-             int hist_cap) {
+             int hist_cap, int wrap_nxp) {
+  // wrap_nxp = nx + 1 with periodic x (column nx repeats column 0 and is left out of
+  // the L2 sum), 0 otherwise
   double mx = 0.0, sm = 0.0;
   const size_t n = (size_t)nif * per_side;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -328,7 +334,7 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
     const size_t j = e / per_side, r = e - j * per_side;
     const double d = bands[(j * 2 + 0) * per_side + r] - bands[(j * 2 + 1) * per_side + r];
     mx = nan_max(mx, fabs(d));
-    sm += d * d;
+    if (wrap_nxp == 0 || (int)(r % (size_t)wrap_nxp) != wrap_nxp - 1) sm += d * d;
   }
   block_reduce(mx, sm);
   double emis = 0.0, ssum = 0.0;
@@ -342,6 +348,26 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
     hist[3 * slot + 2] = scal[2];
     *iter = it + 1;
   }
+}
+
+// Periodic x on a padded [nrows][P] array (column m at m+1): column nx repeats
+// column 0, and the ghost columns -1 and nx+1 hold columns nx-1 and 1, so that the
+// halo lanes of the next pass see the wrapped upwind neighbours.  Needs nx >= 2.
+template <typename T>
+__global__ void periodic_wrap_kernel(T* __restrict__ a, int nrows, int P, int nx) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    T* row = a + (size_t)r * P;
+    const T c0 = row[1], c1 = row[2], clast = row[nx];
+    row[0] = clast;
+    row[nx + 1] = c0;
+    row[nx + 2] = c1;
+  }
+}
+
+// Periodic x on interface data [lines][nx+1]: column nx repeats column 0.
+__global__ void periodic_trace_kernel(double* __restrict__ lam, size_t lines, int nx) {
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < lines; l += (size_t)gridDim.x * blockDim.x)
+    lam[l * (nx + 1) + nx] = lam[l * (nx + 1)];
 }
 
 // u(T) assembled from the strips: row i taken from row_of[i] of UT.

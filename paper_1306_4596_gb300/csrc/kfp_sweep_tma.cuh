@@ -162,7 +162,7 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
         lam = st.p_bot * (double)u_m1 + d * A.inv_2hv;
       } else {
         lam = (st.p_bot + st.q_bot) * (double)u -
-              A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
+              A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
       }
       A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
     }
@@ -182,13 +182,13 @@ __device__ __forceinline__ T special_row(const PassArgs<T>& A, const StripInfo& 
     case 3:
       return in_dom ? (T)A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : T(0);
     case 4:
-      return in_dom ? (T)A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : T(0);
+      return in_dom ? (T)A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : T(0);
     case 5: {
       const double lam = in_dom ? A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : 0.0;
       return (T)((double)regular + (double)glam * lam);
     }
     case 6: {
-      const double lam = in_dom ? A.lam_in[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : 0.0;
+      const double lam = in_dom ? A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : 0.0;
       return (T)((double)regular + (double)glam * lam);
     }
     default:
@@ -461,7 +461,7 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
   init_ring(sm);
-  (void)pass_unit<T, UP, MODE, FMODE, NST>(maps, X, k, blockIdx.y, blockIdx.x, sm, 0u);
+  (void)pass_unit<T, UP, MODE, FMODE, NST>(maps, X, k, blockIdx.y + X.p.strip0, blockIdx.x, sm, 0u);
 }
 
 // ---------------------------------------------------------------------------

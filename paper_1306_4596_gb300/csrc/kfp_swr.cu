@@ -45,6 +45,7 @@ thread_local std::string g_create_error;
 struct Geometry {
   double x0, x1, v0, v1, dt, hx, hv, r;
   int nx, nv, nt, S, ov, robin, P, W, Lmax, rows, nforce;
+  int neumann, periodic;  // zero flux in v, periodic in x (Section 6.1)
   std::vector<double> p, q;
   std::vector<kfp::StripInfo> strips;
   std::vector<int> row_of;  // [nv+1] row of UT holding node i at t = T
@@ -89,6 +90,9 @@ kfp_status build_geometry(const kfp_swr_desc* d, int nforce, Geometry* g, std::s
   g->nx = d->nx; g->nv = d->nv; g->nt = d->nt; g->S = S; g->ov = ov;
   g->robin = (d->tc == KFP_ROBIN) ? 1 : 0;
   g->nforce = nforce;
+  g->neumann = (d->flags & KFP_FLAG_NEUMANN_V) ? 1 : 0;
+  g->periodic = (d->flags & KFP_FLAG_PERIODIC_X) ? 1 : 0;
+  if (g->periodic && d->nx < 2) return bad(KFP_EINVAL, "periodic x needs nx >= 2");
   g->hx = (d->x1 - d->x0) / d->nx;
   g->hv = (d->v1 - d->v0) / d->nv;
   g->r = d->dt / (g->hv * g->hv);
@@ -146,11 +150,13 @@ std::vector<double> build_factors(const Geometry& g) {
       for (int l = 0; l < L; ++l) {
         const int i = st.lo + l;
         const double vi = g.v0 + i * g.hv;
-        const bool inflow = (kappa == 0 && vi > 0) || (kappa == 2 && vi < 0);
+        const bool inflow = !g.periodic && ((kappa == 0 && vi > 0) || (kappa == 2 && vi < 0));
         const bool top = st.has_top && i == st.hi;
         const bool bot = st.has_bot && i == st.lo;
         a[l] = 0.0; b[l] = 1.0; c[l] = 0.0;
-        if (i == 0 || i == g.nv || inflow) continue;            // identity rows
+        if ((!g.neumann && (i == 0 || i == g.nv)) || inflow) continue;  // identity rows
+        if (i == 0) { b[l] = 1 + 2 * r; c[l] = -2 * r; continue; }      // zero-flux half cells
+        if (i == g.nv) { a[l] = -2 * r; b[l] = 1 + 2 * r; continue; }
         if (top || bot) {
           if (!g.robin) continue;                               // Dirichlet: identity
           if (top) { a[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.p_top * g.dt / g.hv; }
@@ -272,13 +278,17 @@ struct kfp_swr {
   }
 
   size_t elem() const { return prec == KFP_F64 ? sizeof(double) : sizeof(float); }
-  int launches_per_iter() const { return g.nt + 1 + 2; }
+  int launches_per_iter() const {
+    const int groups = (flags & KFP_FLAG_GAUSS_SEIDEL) ? g.S : 1;
+    return (g.nt + 1 + (g.periodic ? g.nt : 0)) * groups + 2;
+  }
 
   template <typename T>
   kfp::PassArgs<T> pass_args() const {
     kfp::PassArgs<T> A;
     A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.S = g.S; A.ov = g.ov; A.P = g.P; A.W = g.W;
     A.Lmax = g.Lmax; A.nforce = g.nforce; A.robin = g.robin;
+    A.neumann_v = g.neumann; A.periodic_x = g.periodic;
     A.two_dt_hv = 2.0 * g.dt / g.hv;
     A.inv_2hv = 1.0 / (2.0 * g.hv);
     A.strips = strips;
@@ -291,6 +301,8 @@ struct kfp_swr {
     A.bc_xin = bc_xin;
     A.bc_v = bc_v;
     A.lam_in = lam_in;
+    A.lam_bot_src = (flags & KFP_FLAG_GAUSS_SEIDEL) ? lam_next : lam_in;
+    A.strip0 = 0;
     A.lam_next = lam_next;
     A.bands = bands;
     A.Y0 = (T*)Y0;
@@ -307,17 +319,37 @@ struct kfp_swr {
       else enqueue_passes_tma<T, 2>(st);
       return;
     }
-    const kfp::PassArgs<T> A = pass_args<T>();
-    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
+    kfp::PassArgs<T> A = pass_args<T>();
+    // parallel form: all strips in every launch; serial form: one strip at a time, in
+    // increasing order, so that each reads the data the strip below just produced
+    const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+    const int groups = serial ? g.S : 1;
+    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
     const dim3 block(kfp::kWarpsPerBlock * 32);
-    // pass k runs in ascending row order when k is even (step 1 is factored upward)
-    kfp::sweep_pass_kernel<T, true, 0><<<grid, block, 0, st>>>(A, 0);
-    for (int k = 1; k < g.nt; ++k) {
-      if (k & 1) kfp::sweep_pass_kernel<T, false, 1><<<grid, block, 0, st>>>(A, k);
-      else       kfp::sweep_pass_kernel<T, true, 1><<<grid, block, 0, st>>>(A, k);
+    for (int grp = 0; grp < groups; ++grp) {
+      A.strip0 = serial ? grp : 0;
+      // pass k runs in ascending row order when k is even (step 1 is factored upward)
+      kfp::sweep_pass_kernel<T, true, 0><<<grid, block, 0, st>>>(A, 0);
+      wrap_after_pass<T>(st, 0, A.strip0, serial ? 1 : g.S);
+      for (int k = 1; k < g.nt; ++k) {
+        if (k & 1) kfp::sweep_pass_kernel<T, false, 1><<<grid, block, 0, st>>>(A, k);
+        else       kfp::sweep_pass_kernel<T, true, 1><<<grid, block, 0, st>>>(A, k);
+        wrap_after_pass<T>(st, k, A.strip0, serial ? 1 : g.S);
+      }
+      if (g.nt & 1) kfp::sweep_pass_kernel<T, false, 2><<<grid, block, 0, st>>>(A, g.nt);
+      else          kfp::sweep_pass_kernel<T, true, 2><<<grid, block, 0, st>>>(A, g.nt);
     }
-    if (g.nt & 1) kfp::sweep_pass_kernel<T, false, 2><<<grid, block, 0, st>>>(A, g.nt);
-    else          kfp::sweep_pass_kernel<T, true, 2><<<grid, block, 0, st>>>(A, g.nt);
+  }
+
+  // Periodic x: after pass k wrote y^{k+1} of strips [s0, s0 + ns), refresh column nx
+  // and the ghost columns of those rows for the halo lanes of pass k+1.
+  template <typename T>
+  void wrap_after_pass(cudaStream_t st, int k, int s0, int ns) const {
+    if (!g.periodic) return;
+    T* Yn = (T*)(((k + 1) & 1) ? Y1 : Y0);
+    const int r0 = g.strips[s0].rowoff;
+    const int r1 = (s0 + ns < g.S) ? g.strips[s0 + ns].rowoff : g.rows;
+    kfp::periodic_wrap_kernel<T><<<(r1 - r0 + 255) / 256, 256, 0, st>>>(Yn + (size_t)r0 * g.P, r1 - r0, g.P, g.nx);
   }
 
   template <typename T>
@@ -328,17 +360,24 @@ struct kfp_swr {
   template <typename T, int FM>
   void enqueue_passes_tma(cudaStream_t st) const {
     constexpr int NST = tma_stages<T>();
-    const kfp::TmaArgs<T> X = tma_args<T>();
-    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
+    kfp::TmaArgs<T> X = tma_args<T>();
+    const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+    const int groups = serial ? g.S : 1;
+    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
     const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
     const size_t sm = tma_smem_bytes<T>();
-    kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<grid, block, sm, st>>>(maps, X, 0);
-    for (int k = 1; k < g.nt; ++k) {
-      if (k & 1) kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
-      else       kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+    for (int grp = 0; grp < groups; ++grp) {
+      X.p.strip0 = serial ? grp : 0;
+      kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<grid, block, sm, st>>>(maps, X, 0);
+      wrap_after_pass<T>(st, 0, X.p.strip0, serial ? 1 : g.S);
+      for (int k = 1; k < g.nt; ++k) {
+        if (k & 1) kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+        else       kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+        wrap_after_pass<T>(st, k, X.p.strip0, serial ? 1 : g.S);
+      }
+      if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
+      else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
     }
-    if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
-    else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
   }
 
   template <typename T, int FM>
@@ -390,7 +429,7 @@ struct kfp_swr {
     if (g.S > 1 && kind != kInner) {
       kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
           bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
-          scal, hist, iter, hist_cap);
+          scal, hist, iter, hist_cap, g.periodic ? g.nx + 1 : 0);
     }
     record(3, st, capturing);
   }
@@ -402,7 +441,7 @@ struct kfp_swr {
                                                                           tickets + 0, scal);
     kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
         bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1, scal, hist, iter,
-        hist_cap);
+        hist_cap, g.periodic ? g.nx + 1 : 0);
   }
 
   template <typename T>
@@ -412,7 +451,7 @@ struct kfp_swr {
     X.rows = g.rows;
     X.Lpad = Lpad;
     X.flag = flag;
-    X.bc_data = (bc_xin || bc_v) ? 1 : 0;
+    X.bc_data = ((bc_xin && !g.periodic) || (bc_v && !g.neumann)) ? 1 : 0;
     return X;
   }
 
@@ -662,6 +701,17 @@ kfp_status upload_padded(kfp_swr* h, const double* src, int rows, int on_device,
   return KFP_OK;
 }
 
+// Periodic x: column nx of interface data [.][nx+1] repeats column 0.
+kfp_status wrap_traces(kfp_swr* h, double* lam) {
+  if (!h->g.periodic || h->n_trace == 0) return KFP_OK;
+  const size_t lines = h->n_trace / (h->g.nx + 1);
+  kfp::periodic_trace_kernel<<<(int)std::min<size_t>((lines + 255) / 256, 4096), 256, 0, h->stream>>>(lam, lines,
+                                                                                                     h->g.nx);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "periodic trace wrap failed: %s", cudaGetErrorString(e));
+  return KFP_OK;
+}
+
 kfp_status alloc(kfp_swr* h, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
@@ -740,9 +790,9 @@ kfp_status build_records(kfp_swr* h, const std::vector<double>& coef, const std:
           const int i = st.lo + l;
           const double vi = g.v0 + i * g.hv;
           const double cab = std::fabs(vi * g.dt / g.hx);
-          const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
+          const bool inflow = !g.periodic && ((cls == 0 && vi > 0) || (cls == 2 && vi < 0));
           int kind = 0;
-          if (i == 0 || i == g.nv) kind = 2;
+          if (!g.neumann && (i == 0 || i == g.nv)) kind = 2;
           else if (inflow) kind = 1;
           else if (st.has_top && i == st.hi) kind = g.robin ? 5 : 3;
           else if (st.has_bot && i == st.lo) kind = g.robin ? 6 : 4;
@@ -771,11 +821,11 @@ kfp_status build_records(kfp_swr* h, const std::vector<double>& coef, const std:
           const int i = st.lo + l;
           T* row = &(*gf_out)[((size_t)dir * g.rows + st.rowoff + l) * g.P];
           const double vi = g.v0 + i * g.hv;
-          const bool vbnd = (i == 0 || i == g.nv);
+          const bool vbnd = !g.neumann && (i == 0 || i == g.nv);
           const bool dir_if = !g.robin && ((st.has_top && i == st.hi) || (st.has_bot && i == st.lo));
           for (int m = 0; m <= g.nx; ++m) {
             const int cls = m == 0 ? 0 : (m == g.nx ? 2 : 1);
-            const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
+            const bool inflow = !g.periodic && ((cls == 0 && vi > 0) || (cls == 2 && vi < 0));
             const double gE = coef[(((size_t)s * 3 + cls) * 2 + dir) * 3 * Lm + l];
             row[m + 1] = (vbnd || inflow || dir_if) ? T(0) : (T)(gE * (g.dt * a0) * Fh[(size_t)i * nxp + m]);
           }
@@ -806,6 +856,8 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
       Fh.resize((size_t)(g.nv + 1) * nxp);
       KFP_CUDA_TRY_H(cudaMemcpy(Fh.data(), pb->f_space, sizeof(double) * Fh.size(),
                                 pb->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      if (g.periodic)  // node nx repeats node 0
+        for (int i = 0; i <= g.nv; ++i) Fh[(size_t)i * nxp + g.nx] = Fh[(size_t)i * nxp];
     }
   }
   h->Lpad = g.Lmax + 2 * kfp::kRecPad;
@@ -871,6 +923,17 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   for (int r = 0; r < g.nforce; ++r)
     TRY(upload_padded(h, pb->f_space + (size_t)r * (g.nv + 1) * nxp, g.nv + 1, pb->on_device,
                       (char*)h->F + (size_t)r * (g.nv + 1) * g.P * es));
+  if (g.periodic) {  // column nx repeats column 0; ghost columns for the first pass
+    const int fr = std::max(g.nforce, 1) * (g.nv + 1);
+    if (h->prec == KFP_F64) {
+      kfp::periodic_wrap_kernel<double><<<(g.nv + 256) / 256, 256, 0, h->stream>>>((double*)h->U0, g.nv + 1, g.P, g.nx);
+      kfp::periodic_wrap_kernel<double><<<(fr + 255) / 256, 256, 0, h->stream>>>((double*)h->F, fr, g.P, g.nx);
+    } else {
+      kfp::periodic_wrap_kernel<float><<<(g.nv + 256) / 256, 256, 0, h->stream>>>((float*)h->U0, g.nv + 1, g.P, g.nx);
+      kfp::periodic_wrap_kernel<float><<<(fr + 255) / 256, 256, 0, h->stream>>>((float*)h->F, fr, g.P, g.nx);
+    }
+    KFP_CUDA_TRY_H(cudaGetLastError());
+  }
 
   // dt * a_r(t^n), [nt+1][nforce]
   {
@@ -949,6 +1012,7 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   cudaMemsetAsync(h->bands, 0, sizeof(double) * h->n_band, h->stream);
   if (pb->lambda0) TRY(copy_in(h, h->lam_in, pb->lambda0, sizeof(double) * h->n_trace, pb->on_device));
   else cudaMemsetAsync(h->lam_in, 0, sizeof(double) * h->n_trace, h->stream);
+  TRY(wrap_traces(h, h->lam_in));
 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1056,8 +1120,10 @@ std::vector<double> build_adjoint_factors(const Geometry& g) {
 kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
                          double* grad_q) {
   Geometry& g = h->g;
-  if (!g.robin || g.ov != 0 || g.S < 2 || h->prec != KFP_F64 || h->inner)
-    return h->fail(KFP_ENOTSUP, "the adjoint needs FP64, Robin transmission, no overlap and >= 2 strips");
+  if (!g.robin || g.ov != 0 || g.S < 2 || h->prec != KFP_F64 || h->inner || (h->flags & KFP_FLAG_GAUSS_SEIDEL) ||
+      g.neumann || g.periodic)
+    return h->fail(KFP_ENOTSUP,
+                   "the adjoint needs FP64, Robin transmission, no overlap, >= 2 strips and the parallel form");
   if (K < 1) return h->fail(KFP_EINVAL, "need K >= 1");
   const size_t nxp = g.nx + 1, per = (size_t)g.nt * nxp, ntr = h->n_trace;
   const size_t field = (size_t)g.rows * nxp;
@@ -1493,6 +1559,7 @@ kfp_status kfp_swr_set_traces(kfp_swr_t h, const double* src, int src_on_device)
   if (!src) return h->fail(KFP_EINVAL, "src is NULL");
   if (h->n_trace == 0) return KFP_OK;
   kfp_status rc = copy_in(h, h->lam_in, src, sizeof(double) * h->n_trace, src_on_device);
+  if (!rc) rc = wrap_traces(h, h->lam_in);
   if (rc) return rc;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(KFP_ECUDA, "sync failed");
   return KFP_OK;
@@ -1609,6 +1676,16 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
     if (descs[i].prec != b->prec) {
       g_batch_create_error = "all problems of a batch need the same precision";
       rc = KFP_EINVAL;
+      break;
+    }
+    if (descs[i].flags & KFP_FLAG_GAUSS_SEIDEL) {
+      g_batch_create_error = "the batched sweep runs the parallel form only";
+      rc = KFP_ENOTSUP;
+      break;
+    }
+    if (descs[i].flags & (KFP_FLAG_NEUMANN_V | KFP_FLAG_PERIODIC_X)) {
+      g_batch_create_error = "the batched sweep takes Dirichlet data in x and v only";
+      rc = KFP_ENOTSUP;
       break;
     }
     kfp_swr_desc d = descs[i];

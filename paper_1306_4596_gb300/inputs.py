@@ -226,6 +226,26 @@ def adjoint_workload(seed: int = 5) -> Problem:
     return gaussian_bumps(512, 1024, 500, 4e-4, nstrips=8, p=4.0, seed=seed)
 
 
+def model_error_equation(j: int = 0, overlap: int = 3, robin: bool = True, p=4.23, q=None, seed: int = 7,
+                         T: float = 2.0, nstrips: int = 2) -> Problem:
+    """Error equation of the model problem of Section 6.1 in the setting of Section 6.4 and
+    Table 1: x in [0,1] periodic, v in [-1,1] with zero flux, f = 0, u0 = 0, T = 2,
+    hx = hv = dt = 0.01 * 2^-j (so nx = 100 * 2^j, nv = nt = 200 * 2^j), strips split
+    at v = 0, random initial data lambda_1^0 ~ U[-1,1] (default_rng(seed), one draw of
+    shape [S-1][nt][nx+1]) and lambda_2^0 = 0."""
+    n = 100 * 2 ** j
+    h = 1.0 / n
+    nx, nv, nt = n, 2 * n, int(round(T / h))
+    rng = np.random.default_rng(seed)
+    lam0 = np.zeros((nstrips - 1, 2, nt, nx + 1))
+    lam0[:, 0] = rng.uniform(-1, 1, (nstrips - 1, nt, nx + 1))
+    pp, qq = _pq(nstrips, p, q)
+    return Problem(0.0, 1.0, -1.0, 1.0, h, nx, nv, nt, nstrips, overlap, robin, pp, qq,
+                   np.zeros((nv + 1, nx + 1)), np.zeros((1, nt + 1)), np.zeros((1, nv + 1, nx + 1)),
+                   None, None, lam0, neumann_v=True, periodic_x=True,
+                   name=f"model error equation j={j} ov={overlap} {'Robin' if robin else 'Dirichlet'}")
+
+
 def batch_instances(count: int = 256, seed_base: int = 3000, v_range=(-4.0, 4.0)) -> List[Problem]:
     """Uneven instances for the batched form.  Instance i uses rng = default_rng(seed_base + i)
     and draws, in order: nx ~ U{128..1024}; S ~ U{2,4,8,16}; cells per strip

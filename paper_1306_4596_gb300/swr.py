@@ -23,7 +23,15 @@ STATUS_NAMES = {0: "KFP_OK", 1: "KFP_EINVAL", 2: "KFP_ECFL", 3: "KFP_ENOMEM", 4:
 KFP_DIRICHLET, KFP_ROBIN = 0, 1
 KFP_F64, KFP_F32, KFP_MIXED = 0, 1, 2
 PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
-KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC = 1, 2, 4
+KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1, 2, 4, 8
+KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X = 16, 32
+
+
+def problem_flags(prob) -> int:
+    """Flags that a problem's own definition sets: iteration order and boundary conditions."""
+    return ((KFP_FLAG_GAUSS_SEIDEL if getattr(prob, "gauss_seidel", False) else 0)
+            | (KFP_FLAG_NEUMANN_V if getattr(prob, "neumann_v", False) else 0)
+            | (KFP_FLAG_PERIODIC_X if getattr(prob, "periodic_x", False) else 0))
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
@@ -250,6 +258,7 @@ def _marshal(prob, precision: str, flags: int, inputs_on: str, keep: list):
         return t.data_ptr()
 
     S = prob.nstrips
+    flags |= problem_flags(prob)
     p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
     q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
     keep.extend([p, q])
@@ -375,7 +384,8 @@ class SWR:
         self._p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
         self._q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
         flags = ((0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
-                 | (KFP_FLAG_GENERIC if generic else 0))
+                 | (KFP_FLAG_GENERIC if generic else 0)
+                 | problem_flags(prob))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
                                  self._p.ctypes.data if self._p is not None else None,

@@ -46,6 +46,8 @@ def run_gpu(prob, iters, precision="f64", **kw):
 
 def run_oracle(prob, iters):
     lam = np.zeros(oracle.trace_shape(prob)) if prob.lam0 is None else prob.lam0.copy()
+    if prob.periodic_x:  # node nx repeats node 0, also in the initial interface data
+        lam[..., prob.nx] = lam[..., 0]
     hist = []
     bands = None
     u_T = None
@@ -239,3 +241,80 @@ def test_host_inputs_match_device_inputs():
     b = run_gpu(prob, 2, inputs_on="device")
     for key in ("u_T", "lam", "bands", "hist"):
         assert np.array_equal(a[key], b[key]), key
+
+
+GS_CASES = [
+    ("small_dirichlet", inputs.small_dirichlet, 4),
+    ("small_robin", inputs.small_robin, 4),
+    ("robin_4_strips_ov2_fast", lambda: RD(90, 256, 6, 0.002, 4, 2, True, p=5.0, seed=50, nforce=1,
+                                           boundary_data=False), 3),
+    ("dirichlet_3_strips_bc_data", lambda: RD(37, 24, 7, 0.01, 3, 2, False, seed=51, nforce=1), 3),
+    ("robin_two_terms_plain_kernel", lambda: RD(61, 32, 5, 0.01, 4, 0, True, p=3.0, q=1.5, seed=52, nforce=2), 3),
+]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,iters", GS_CASES, ids=[c[0] for c in GS_CASES])
+def test_gauss_seidel_order_matches_oracle(label, factory, iters, precision):
+    prob = factory().replace(gauss_seidel=True)
+    ref = run_oracle(prob, iters)
+    gpu = run_gpu(prob, iters, precision)
+    (check_f64 if precision == "f64" else check_f32)(gpu, ref, prob)
+
+
+# Model-problem boundary conditions (Section 6.1): zero flux in v and/or periodic x.
+# Column counts put node nx on the first, a middle and the last output lane of a warp
+# (nx = 30, 89, 29 / 119) and at the smallest periodic grid (nx = 2).
+VARIANT_CASES = [
+    ("both_fast_S4_ov0", lambda: RD(119, 256, 6, 0.002, 4, 0, True, p=5.0, seed=60, nforce=1), 3, True, True),
+    ("both_fast_S2_ov3_const", lambda: RD(89, 192, 5, 0.002, 2, 3, True, p=4.0, seed=61, nforce=1,
+                                          constant_in_time=True), 3, True, True),
+    ("both_no_forcing_dirichlet", lambda: RD(30, 128, 5, 0.003, 2, 4, False, seed=62, nforce=0), 3, True, True),
+    ("both_two_terms_plain_kernel", lambda: RD(29, 32, 5, 0.01, 4, 0, True, p=3.0, q=1.5, seed=63,
+                                               nforce=2), 3, True, True),
+    ("both_nx2_single_strip", lambda: RD(2, 16, 4, 0.01, 1, 0, False, seed=64, nforce=1), 1, True, True),
+    ("neumann_with_inflow_data", lambda: RD(61, 64, 5, 0.005, 4, 2, True, p=3.0, seed=65, nforce=1), 3,
+     True, False),
+    ("periodic_with_v_data", lambda: RD(121, 96, 5, 0.004, 3, 1, False, seed=66, nforce=1), 3, False, True),
+    ("bumps_both_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=67), 2, True, True),
+]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,iters,neumann,periodic", VARIANT_CASES, ids=[c[0] for c in VARIANT_CASES])
+def test_model_problem_boundaries_match_oracle(label, factory, iters, neumann, periodic, precision):
+    prob = factory().replace(neumann_v=neumann, periodic_x=periodic)
+    ref = run_oracle(prob, iters)
+    gpu = run_gpu(prob, iters, precision)
+    (check_f64 if precision == "f64" else check_f32)(gpu, ref, prob)
+    if periodic:  # node nx repeats node 0 exactly
+        assert np.array_equal(gpu["u_T"][:, prob.nx], gpu["u_T"][:, 0])
+
+
+@pytest.mark.parametrize("label,factory,iters,neumann,periodic", VARIANT_CASES[:3] + VARIANT_CASES[5:7],
+                         ids=[c[0] for c in VARIANT_CASES[:3] + VARIANT_CASES[5:7]])
+def test_model_problem_boundaries_plain_kernel(label, factory, iters, neumann, periodic):
+    prob = factory().replace(neumann_v=neumann, periodic_x=periodic)
+    check_f64(run_gpu(prob, iters, "f64", generic=True), run_oracle(prob, iters), prob)
+
+
+def test_model_problem_gauss_seidel():
+    prob = RD(119, 256, 6, 0.002, 4, 0, True, p=5.0, seed=68, nforce=1).replace(
+        neumann_v=True, periodic_x=True, gauss_seidel=True)
+    check_f64(run_gpu(prob, 3), run_oracle(prob, 3), prob)
+
+
+def test_model_problem_conserves_mass_on_gpu():
+    """Zero flux in v and periodic x: the converged GPU iterate keeps the discrete mass
+    of u0 (trapezoid weights in v, the nx unique columns in x) to rounding."""
+    prob = inputs.gaussian_bumps(240, 512, 60, 6e-4, 4, p=4.0, seed=69)
+    prob = prob.replace(neumann_v=True, periodic_x=True, f_time=np.zeros_like(prob.f_time))
+    w = np.full(prob.nv + 1, prob.hv)
+    w[0] = w[-1] = 0.5 * prob.hv
+    mass = lambda u: float(w @ u[:, : prob.nx].sum(axis=1)) * prob.hx
+    swr = _swr()
+    with swr.SWR(prob, "f64") as s:
+        s.sweep(200, tol=1e-10)
+        u_T = s.solution()
+    m0 = mass(prob.u0)
+    assert abs(mass(u_T) - m0) <= 1e-11 * abs(m0)
