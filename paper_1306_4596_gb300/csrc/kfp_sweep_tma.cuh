@@ -125,9 +125,12 @@ __device__ __forceinline__ void load_coef4(const float* rc, float& ncp, float& a
 }
 
 // Record the outgoing interface data and the overlap values of u^k at row l.
+// lam_top / lam_bot: the incoming data of this strip at t^k (used by the Robin
+// trace without overlap), loaded once per pass.
 template <typename T, bool UP>
 __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo& st, int s, int k, int l,
-                                           int m, bool out_lane, T u, T u_m1, T u_m2) {
+                                           int m, bool out_lane, T u, T u_m1, T u_m2, double lam_top,
+                                           double lam_bot) {
   const int ov = A.ov, nt = A.nt, nxp = A.nx + 1, lo = st.lo;
   const bool robin_in = A.robin && ov >= 1;
   if (st.has_top) {
@@ -143,7 +146,7 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
         const double d = UP ? ((double)u - (double)u_m2) : ((double)u_m2 - (double)u);
         lam = st.q_top * (double)u_m1 - d * A.inv_2hv;
       } else {
-        lam = (st.p_top + st.q_top) * (double)u - A.lam_in[(((size_t)s * 2 + 0) * nt + (k - 1)) * nxp + m];
+        lam = (st.p_top + st.q_top) * (double)u - lam_top;
       }
       A.lam_next[(((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m] = lam;
     }
@@ -161,8 +164,7 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
         const double d = UP ? ((double)u - (double)u_m2) : ((double)u_m2 - (double)u);
         lam = st.p_bot * (double)u_m1 + d * A.inv_2hv;
       } else {
-        lam = (st.p_bot + st.q_bot) * (double)u -
-              A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
+        lam = (st.p_bot + st.q_bot) * (double)u - lam_bot;
       }
       A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
     }
@@ -170,27 +172,24 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
 }
 
 // Right-hand side override of a non-interior row (kinds 1..6), given the regular value.
+// lam_top / lam_bot: this strip's incoming data at t^{k1} (0 outside the domain).
 template <typename T>
-__device__ __forceinline__ T special_row(const PassArgs<T>& A, const StripInfo& st, int s, int kind, int k1, int i,
-                                      int m, bool in_dom, int inflow_side, T regular, T glam) {
-  const int nxp = A.nx + 1, nt = A.nt;
+__device__ __forceinline__ T special_row(const PassArgs<T>& A, int kind, int k1, int i, int m, bool in_dom,
+                                         int inflow_side, T regular, T glam, double lam_top, double lam_bot) {
+  const int nxp = A.nx + 1;
   switch (kind) {
     case 1:
       return (A.bc_xin && inflow_side >= 0) ? (T)A.bc_xin[((size_t)k1 * 2 + inflow_side) * (A.nv + 1) + i] : T(0);
     case 2:
       return (A.bc_v && in_dom) ? (T)A.bc_v[((size_t)k1 * 2 + (i == 0 ? 0 : 1)) * nxp + m] : T(0);
     case 3:
-      return in_dom ? (T)A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : T(0);
+      return (T)lam_top;
     case 4:
-      return in_dom ? (T)A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : T(0);
-    case 5: {
-      const double lam = in_dom ? A.lam_in[(((size_t)s * 2 + 0) * nt + (k1 - 1)) * nxp + m] : 0.0;
-      return (T)((double)regular + (double)glam * lam);
-    }
-    case 6: {
-      const double lam = in_dom ? A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k1 - 1)) * nxp + m] : 0.0;
-      return (T)((double)regular + (double)glam * lam);
-    }
+      return (T)lam_bot;
+    case 5:
+      return (T)((double)regular + (double)glam * lam_top);
+    case 6:
+      return (T)((double)regular + (double)glam * lam_bot);
     default:
       return regular;
   }
@@ -288,6 +287,25 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
     if (st.has_top) { rloT = st.alpha_top - st.lo - 1; rhiT = st.alpha_top - st.lo + A.ov + 1; }
   }
 
+  // this strip's incoming interface data, one value per lane, loaded once per pass:
+  // at t^{k+1} for the end rows of the system being eliminated, at t^k for the Robin
+  // trace without overlap recorded from u^k
+  double lam_rhs_top = 0.0, lam_rhs_bot = 0.0, lam_rec_top = 0.0, lam_rec_bot = 0.0;
+  if (in_dom) {
+    const size_t nxp = (size_t)A.nx + 1, nt = (size_t)A.nt;
+    const bool rec_in = MODE != 0 && A.robin && A.ov == 0;
+    if (st.has_top) {
+      const double* src = A.lam_in + ((size_t)s * 2 + 0) * nt * nxp + m;
+      if (MODE != 2) lam_rhs_top = src[(size_t)k * nxp];
+      if (rec_in) lam_rec_top = src[(size_t)(k - 1) * nxp];
+    }
+    if (st.has_bot) {
+      const double* src = A.lam_bot_src + ((size_t)(s - 1) * 2 + 1) * nt * nxp + m;
+      if (MODE != 2) lam_rhs_bot = src[(size_t)k * nxp];
+      if (rec_in) lam_rec_bot = src[(size_t)(k - 1) * nxp];
+    }
+  }
+
   T u_prev = T(0), u_m1 = T(0), u_m2 = T(0), y_prev = T(0);
   const int step = UP ? P : -P;
   // Elimination chain of the previous interior chunk, deferred so that it runs
@@ -321,15 +339,14 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
     const int l1 = l0 + kChunk - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
                                            (rloT <= rhiT && !(l1 < rloT || l0 > rhiT)));
-    // Strip-end rows (boundary / interface kinds), recorded rows, rows outside the strip
-    // and caller boundary data go through the general path; every other chunk is a
-    // run of 16 interior rows with no branch.
-    // the upwind side of every row in the chunk (the v = 0 row and chunks that
-    // straddle it go through the general path)
+    // Chunks that reach outside the strip, caller boundary data, and the chunks holding
+    // the v = 0 row or a change of the upwind side go through the general path.  Every
+    // other chunk is a run of 16 rows with no per-row branch: its recorded rows are
+    // written after the back-substitution chain, and the strip's end rows (interface
+    // data) are folded into the chain's first or last term.
     const int sg_first = slot_int(sm.rec[q][0][cls * 8 + 6]);
     const int sg_last = slot_int(sm.rec[q][kChunk - 1][cls * 8 + 6]);
-    const bool general = X.bc_data || rec_chunk || c == 0 || c == NC - 1 || sg_first != sg_last ||
-                         sg_first == 0;
+    const bool general = X.bc_data || l0 < 0 || l1 >= L || sg_first != sg_last || sg_first == 0;
     if (!general) {
       const int src = lane - sg_first;  // upwind neighbour lane for the whole chunk
       const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
@@ -377,6 +394,16 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
         }
       }
       if (MODE != 0) {
+        if (rec_chunk) {
+#pragma unroll
+          for (int t = 0; t < kChunk; ++t) {
+            const int l = UP ? l0 + t : l0 + kChunk - 1 - t;
+            const T um1 = t >= 1 ? uu[t - 1] : u_m1;
+            const T um2 = t >= 2 ? uu[t - 2] : (t == 1 ? u_m1 : u_m2);
+            if ((l >= rloB && l <= rhiB) || (l >= rloT && l <= rhiT))
+              record_row<T, UP>(A, st, s, k, l, m, out_lane, uu[t], um1, um2, lam_rec_top, lam_rec_bot);
+          }
+        }
         u_m2 = uu[kChunk - 2];
         u_m1 = uu[kChunk - 1];
       }
@@ -409,6 +436,21 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
           xx[t] = fma(ca, uu[t], fma(cb, unb, gterm));
           hn[t] = chn;
         }
+        // the strip's first and last rows in pass order carry the interface data
+        // (Dirichlet: the value itself; Robin: g 2dt/hv lambda on top of the regular
+        // right-hand side); v-boundary and x-inflow rows without caller data are zero
+        // rows already
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (e == 0 ? c != 0 : c != NC - 1) continue;
+          const int te = e == 0 ? 0 : kChunk - 1;
+          const int re = UP ? te : (kChunk - 1 - te);
+          const int kind = slot_int(sm.rec[q][re][cls * 8 + 7]);
+          if (kind >= 3) {
+            const double lam = (kind == 3 || kind == 5) ? lam_rhs_top : lam_rhs_bot;
+            xx[te] = kind <= 4 ? (T)lam : (T)((double)xx[te] + (double)sm.rec[q][re][cls * 8 + 5] * lam);
+          }
+        }
         pout = Ynext + (size_t)(st.rowoff + lf) * P + col;
         pend = true;
       }
@@ -426,7 +468,7 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
         } else {
           u = fma(rc[0], u_prev, sm.tile[q][r][wl * kOutCols + lane]);
           u_prev = u;
-          if (rec_chunk) record_row<T, UP>(A, st, s, k, l, m, out_lane, u, u_m1, u_m2);
+          if (rec_chunk) record_row<T, UP>(A, st, s, k, l, m, out_lane, u, u_m1, u_m2, lam_rec_top, lam_rec_bot);
           u_m2 = u_m1;
           u_m1 = u;
           if (MODE == 2) {
@@ -440,7 +482,8 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
         if (FMODE == 2) gterm = (rc[4] * dtak) * sm.frc[q][r][wl * kOutCols + lane];
         T y = fma(rc[3], y_prev, fma(rc[1], u, fma(rc[2], unb, gterm)));
         const int kind = slot_int(rc[7]);
-        if (kind != 0) y = special_row<T>(A, st, s, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[5]);
+        if (kind != 0)
+          y = special_row<T>(A, kind, k1, st.lo + l, m, in_dom, inflow_side, y, rc[5], lam_rhs_top, lam_rhs_bot);
         if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
         y_prev = y;
       }
