@@ -46,7 +46,7 @@ class _Desc(ctypes.Structure):
         ("nx", ctypes.c_int), ("nv", ctypes.c_int), ("nt", ctypes.c_int),
         ("nstrips", ctypes.c_int), ("overlap", ctypes.c_int), ("robin", ctypes.c_int),
         ("p", _dp), ("q", _dp), ("gauss_seidel", ctypes.c_int), ("neumann_v", ctypes.c_int),
-        ("periodic_x", ctypes.c_int),
+        ("periodic_x", ctypes.c_int), ("scheme", ctypes.c_int),
     ]
 
 
@@ -122,7 +122,7 @@ class _Marshalled:
                           S, prob.overlap if overlap is None else overlap,
                           int(prob.robin if robin is None else robin), _ptr(self.p), _ptr(self.q),
                           int(getattr(prob, "gauss_seidel", False)), int(getattr(prob, "neumann_v", False)),
-                          int(getattr(prob, "periodic_x", False)))
+                          int(getattr(prob, "periodic_x", False)), int(getattr(prob, "scheme", 0)))
         self.prob = _Problem(_ptr(self.u0), int(self.f_time.shape[0]), _ptr(self.f_time),
                              _ptr(self.f_space), _ptr(self.bc_xin), _ptr(self.bc_v))
 

@@ -59,6 +59,7 @@ int kfo_validate(const kfo_desc* d) {
   if (!(d->x1 > d->x0) || !(d->v1 > d->v0) || !(d->dt > 0)) return KFO_EINVAL;
   if (d->nv % d->nstrips != 0) return KFO_EINVAL;
   if (d->periodic_x && d->nx < 2) return KFO_EINVAL;
+  if (d->scheme != 0 && !(d->scheme == 1 && d->periodic_x && d->neumann_v)) return KFO_EINVAL;
   if (d->nstrips > 1) {
     int w = cells_per_strip(d);
     if (w < 2 || d->overlap < 0 || d->overlap >= w) return KFO_EINVAL;
@@ -278,6 +279,147 @@ static int solve_strip(const kfo_desc* d, const kfo_problem* pb, int s, const st
   return KFO_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Scheme 1: the Lie splitting of Section 6.2 (P1 elements in v, implicit     */
+/* Euler over dt, then explicit upwind transport over dt), periodic x and     */
+/* zero flux in v, on one strip over the whole window.                      */
+/* ------------------------------------------------------------------------ */
+
+static double forcing_at(const kfo_desc* d, const kfo_problem* pb, int i, int m, int n) {
+  const int nxp = d->nx + 1;
+  double f = 0.0;
+  for (int r = 0; r < pb->nforce; ++r)
+    f += pb->f_time[(size_t)r * (d->nt + 1) + n] * pb->f_space[((size_t)r * (d->nv + 1) + i) * nxp + m];
+  return f;
+}
+
+static int solve_strip_fe(const kfo_desc* d, const kfo_problem* pb, int s, const strip_io* io,
+                          double* u_T_strip) {
+  const int S = d->nstrips, nx = d->nx, nxp = d->nx + 1, nt = d->nt, ov = d->overlap;
+  const int lo = strip_lo(d, s), hi = strip_hi(d, s), L = hi - lo + 1;
+  const double h = hv_of(d), dt = d->dt, hx = hx_of(d);
+  const int has_bot = s > 0, has_top = s < S - 1;
+  /* entries of M/dt + S (full row, half row at an end node, off-diagonal) and of M */
+  const double k_full = 2.0 * h / (3.0 * dt) + 2.0 / h;
+  const double k_half = h / (3.0 * dt) + 1.0 / h;
+  const double k_off = h / (6.0 * dt) - 1.0 / h;
+  const double m_full = 2.0 * h / 3.0, m_half = h / 3.0, m_off = h / 6.0;
+
+  double* un = (double*)malloc(sizeof(double) * (size_t)L * nxp);
+  double* w = (double*)malloc(sizeof(double) * (size_t)L * nxp);
+  double* z = (double*)malloc(sizeof(double) * (size_t)L * nxp);
+  double* a = (double*)malloc(sizeof(double) * (size_t)L);
+  double* b = (double*)malloc(sizeof(double) * (size_t)L);
+  double* c = (double*)malloc(sizeof(double) * (size_t)L);
+  double* R = (double*)malloc(sizeof(double) * (size_t)L);
+  double* x = (double*)malloc(sizeof(double) * (size_t)L);
+  if (!un || !w || !z || !a || !b || !c || !R || !x) {
+    free(un); free(w); free(z); free(a); free(b); free(c); free(R); free(x);
+    return KFO_ENOMEM;
+  }
+  for (int l = 0; l < L; ++l) {
+    memcpy(un + (size_t)l * nxp, pb->u0 + (size_t)(lo + l) * nxp, sizeof(double) * nxp);
+    un[(size_t)l * nxp + nx] = un[(size_t)l * nxp + 0]; /* node nx repeats node 0 */
+  }
+  if (io->u_all) memcpy(io->u_all, un, sizeof(double) * (size_t)L * nxp);
+#define Z(l, m) z[(size_t)(l) * nxp + (m)]
+#define W(l, m) w[(size_t)(l) * nxp + (m)]
+  for (int n = 0; n < nt; ++n) {
+    /* step 1: (M/dt + S) w = M z, z = u^n / dt + f^{n+1}, column by column */
+    for (int l = 0; l < L; ++l)
+      for (int m = 0; m < nx; ++m) Z(l, m) = un[(size_t)l * nxp + m] / dt + forcing_at(d, pb, lo + l, m, n + 1);
+    for (int m = 0; m < nx; ++m) {
+      for (int l = 0; l < L; ++l) {
+        a[l] = k_off; b[l] = k_full; c[l] = k_off;
+        if (l == 0) a[l] = 0.0;
+        if (l == L - 1) c[l] = 0.0;
+        if (l == 0 && l == L - 1) R[l] = m_half * Z(l, m);
+        else if (l == 0) R[l] = m_half * Z(l, m) + m_off * Z(l + 1, m);
+        else if (l == L - 1) R[l] = m_half * Z(l, m) + m_off * Z(l - 1, m);
+        else R[l] = m_off * Z(l - 1, m) + m_full * Z(l, m) + m_off * Z(l + 1, m);
+        if (l == 0 || l == L - 1) b[l] = k_half; /* end node: one element only */
+      }
+      /* transmission rows (SWR1 / SWR3): Robin adds p or q to the end row, lambda to its
+       * right-hand side; Dirichlet sets the end value */
+      if (has_top) {
+        const double lam = io->lam_top ? io->lam_top[(size_t)n * nxp + m] : 0.0;
+        if (d->robin) { b[L - 1] += d->p[s]; R[L - 1] += lam; }
+        else { a[L - 1] = 0.0; b[L - 1] = 1.0; R[L - 1] = lam; }
+      }
+      if (has_bot) {
+        const double lam = io->lam_bot ? io->lam_bot[(size_t)n * nxp + m] : 0.0;
+        if (d->robin) { b[0] += d->q[s - 1]; R[0] += lam; }
+        else { c[0] = 0.0; b[0] = 1.0; R[0] = lam; }
+      }
+      int rc = kfo_thomas(L, a, b, c, R, x);
+      if (rc) {
+        free(un); free(w); free(z); free(a); free(b); free(c); free(R); free(x);
+        return rc;
+      }
+      for (int l = 0; l < L; ++l) W(l, m) = x[l];
+    }
+    for (int l = 0; l < L; ++l) { W(l, nx) = W(l, 0); Z(l, nx) = Z(l, 0); }
+
+    /* SWR2 / SWR4 from the diffusion step's solution w */
+    for (int m = 0; m <= nx; ++m) {
+      const int mi = m == nx ? 0 : m;
+      if (has_top && io->out_top) { /* lambda_2 of interface s at alpha_s */
+        const int al = alpha_node(d, s) - lo;
+        double lam;
+        if (!d->robin)
+          lam = W(al, m);
+        else if (ov >= 1) /* q w minus the residual of the lower half of row alpha */
+          lam = d->q[s] * W(al, m) -
+                (k_half * W(al, m) + k_off * W(al - 1, m) - m_half * Z(al, m) - m_off * Z(al - 1, m));
+        else
+          lam = (d->p[s] + d->q[s]) * W(al, m) - (io->lam_top ? io->lam_top[(size_t)n * nxp + mi] : 0.0);
+        io->out_top[(size_t)n * nxp + m] = lam;
+      }
+      if (has_bot && io->out_bot) { /* lambda_1 of interface s-1 at beta_{s-1} */
+        const int be = beta_node(d, s - 1) - lo;
+        double lam;
+        if (!d->robin)
+          lam = W(be, m);
+        else if (ov >= 1) /* p w minus the residual of the upper half of row beta */
+          lam = d->p[s - 1] * W(be, m) -
+                (k_half * W(be, m) + k_off * W(be + 1, m) - m_half * Z(be, m) - m_off * Z(be + 1, m));
+        else
+          lam = (d->p[s - 1] + d->q[s - 1]) * W(be, m) -
+                (io->lam_bot ? io->lam_bot[(size_t)n * nxp + mi] : 0.0);
+        io->out_bot[(size_t)n * nxp + m] = lam;
+      }
+    }
+
+    /* step 2: explicit upwind transport of w over dt, periodic in x:
+       w_t + v w_x = 0 with the difference taken on the side the flow comes from */
+    for (int l = 0; l < L; ++l) {
+      const double vi = v_node(d, lo + l), cfl = vi * dt / hx;
+      for (int m = 0; m < nx; ++m) {
+        double u;
+        if (vi > 0) u = W(l, m) - cfl * (W(l, m) - W(l, (m - 1 + nx) % nx));
+        else if (vi < 0) u = W(l, m) - cfl * (W(l, (m + 1) % nx) - W(l, m));
+        else u = W(l, m);
+        un[(size_t)l * nxp + m] = u;
+      }
+      un[(size_t)l * nxp + nx] = un[(size_t)l * nxp + 0];
+    }
+    for (int m = 0; m <= nx; ++m)
+      for (int k = 0; k <= ov; ++k) {
+        if (has_top && io->band_top)
+          io->band_top[((size_t)n * (ov + 1) + k) * nxp + m] = un[(size_t)(alpha_node(d, s) + k - lo) * nxp + m];
+        if (has_bot && io->band_bot)
+          io->band_bot[((size_t)n * (ov + 1) + k) * nxp + m] =
+              un[(size_t)(alpha_node(d, s - 1) + k - lo) * nxp + m];
+      }
+    if (io->u_all) memcpy(io->u_all + (size_t)(n + 1) * L * nxp, un, sizeof(double) * (size_t)L * nxp);
+  }
+#undef Z
+#undef W
+  if (u_T_strip) memcpy(u_T_strip, un, sizeof(double) * (size_t)L * nxp);
+  free(un); free(w); free(z); free(a); free(b); free(c); free(R); free(x);
+  return KFO_OK;
+}
+
 /* Owner of node i at t = T: the lower strip of interface j for i <= I_j. */
 static int owner_strip(const kfo_desc* d, int i) {
   int s = 0;
@@ -317,7 +459,7 @@ int kfo_swr_iteration(const kfo_desc* d, const kfo_problem* pb, const double* la
       uT[s] = (double*)malloc(sizeof(double) * (size_t)L * nxp);
       if (!uT[s]) { rc = KFO_ENOMEM; break; }
     }
-    rc = solve_strip(d, pb, s, &io, uT[s]);
+    rc = d->scheme == 1 ? solve_strip_fe(d, pb, s, &io, uT[s]) : solve_strip(d, pb, s, &io, uT[s]);
   }
   if (rc == KFO_OK && u_T) {
     for (int i = 0; i <= d->nv; ++i) {
@@ -401,7 +543,7 @@ int kfo_monolithic(const kfo_desc* d, const kfo_problem* pb, double* u_T, double
   strip_io io;
   memset(&io, 0, sizeof io);
   io.u_all = u_all;
-  return solve_strip(&one, pb, 0, &io, u_T);
+  return one.scheme == 1 ? solve_strip_fe(&one, pb, 0, &io, u_T) : solve_strip(&one, pb, 0, &io, u_T);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -534,7 +676,7 @@ int kfo_swr_adjoint(const kfo_desc* d, const kfo_problem* pb, const double* lam0
                     double* grad_p, double* grad_q) {
   int rc = kfo_validate(d);
   if (rc) return rc;
-  if (!d->robin || d->overlap != 0 || d->nstrips < 2 || K < 1 || d->gauss_seidel || d->neumann_v ||
+  if (!d->robin || d->overlap != 0 || d->nstrips < 2 || K < 1 || d->gauss_seidel || d->neumann_v || d->scheme ||
       d->periodic_x)
     return KFO_EINVAL;
   const int S = d->nstrips, nxp = d->nx + 1, nt = d->nt;

@@ -26,6 +26,17 @@
  *   Robin rows  half-cell finite-volume rows for (p + d/dv) u = lambda_1 at the
  *               lower strip's top node and (q - d/dv) u = lambda_2 at the upper
  *               strip's bottom node.
+ * Scheme 1 (Section 6.2, Lie splitting with P1 finite elements in v):
+ *   step 1      (M/dt + S) w = M (u^n/dt + f^{n+1}) per column, M and S the P1 mass and
+ *               stiffness matrices (exact integrals; zero flux is the natural condition
+ *               at v0 and v1); Robin ends add p (top) or q (bottom) to the end row's
+ *               diagonal and lambda to its right-hand side; Dirichlet ends set w = lambda.
+ *   step 2      u^{n+1} = w - c_i (w_m - w_{m-1}) for v_i > 0 and w - c_i (w_{m+1} - w_m) for
+ *               v_i < 0, c_i = |v_i| dt / hx (periodic in x).
+ *   traces      from w: Dirichlet w; Robin without overlap (p+q) w - lambda_in; Robin with
+ *               overlap, p w (resp. q w) minus the half-row residual of the strip that
+ *               holds the node inside it (the discrete flux that makes the converged
+ *               iterate the single-domain solution).
  * Every call runs on the calling thread, allocates with malloc and frees before
  * returning.  Return value 0 = success, negative = invalid input (see below).
  */
@@ -51,6 +62,10 @@ typedef struct {
                           Section 6.1) instead of Dirichlet data; bc_v is ignored */
   int periodic_x;      /* 1: x periodic (Section 6.1): nodes m = 0..nx-1 are the unknowns,
                           node nx repeats node 0; bc_xin is ignored */
+  int scheme;          /* 0: implicit Euler in v with upwind transport at t^n (finite volumes,
+                          the default); 1: the Lie splitting of Section 6.2 -- implicit Euler
+                          with P1 finite elements in v over dt, then explicit upwind transport
+                          over dt (model problem only: needs periodic_x and neumann_v) */
 } kfo_desc;
 
 typedef struct {

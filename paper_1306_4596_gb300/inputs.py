@@ -54,6 +54,8 @@ class Problem:
     gauss_seidel: bool = False  # serial SWR1-SWR4 order instead of the parallel form
     neumann_v: bool = False     # homogeneous Neumann at v0, v1 (Section 6.1) instead of Dirichlet data
     periodic_x: bool = False    # periodic in x (Section 6.1): node nx repeats node 0
+    scheme: int = 0             # 0: implicit Euler + upwind (finite volumes in v); 1: the Lie
+                                # splitting of Section 6.2 with P1 elements in v (model problem)
 
     @property
     def hx(self) -> float:

@@ -63,13 +63,13 @@ def _kolmogorov_gaussian(x, v, t, mean0, cov0):
     return scale * np.exp(-0.5 * quad)
 
 
-def _gaussian_problem(nx, nv, T, cfl, nstrips=1, robin=True, p=4.0, overlap=0):
+def _gaussian_problem(nx, nv, T, cfl, nstrips=1, robin=True, p=4.0, overlap=0, vbar=1.0):
     v0, v1 = -4.0, 4.0
     hx = 1.0 / nx
     dt0 = cfl * hx / 4.0
     nt = int(math.ceil(T / dt0))
     dt = T / nt
-    mean0, cov0 = (0.35, 1.0), np.diag([0.05 ** 2, 0.2 ** 2])
+    mean0, cov0 = (0.35 if vbar > 0 else 0.65, vbar), np.diag([0.05 ** 2, 0.2 ** 2])
     x = np.arange(nx + 1) * hx
     v = v0 + np.arange(nv + 1) * ((v1 - v0) / nv)
     u0 = _kolmogorov_gaussian(x, v, 0.0, mean0, cov0)
@@ -704,3 +704,120 @@ def test_model_problem_trace_map_fixed_point(robin, overlap):
     lam_star = np.linalg.solve(np.eye(len(c)) - M, c).reshape(oracle.trace_shape(prob))
     _, _, u_T = oracle.swr_iteration(prob, lam_star)
     np.testing.assert_allclose(u_T, _dense_variants(prob)[-1], rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Scheme of Section 6.2: Lie splitting, P1 elements in v, upwind transport
+# ---------------------------------------------------------------------------
+
+def _p1_matrices(nv, h):
+    """P1 mass and stiffness matrices on a uniform grid of nv elements, assembled
+    element by element (zero flux is the natural boundary condition)."""
+    M = np.zeros((nv + 1, nv + 1))
+    K = np.zeros((nv + 1, nv + 1))
+    for e in range(nv):
+        idx = [e, e + 1]
+        M[np.ix_(idx, idx)] += h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
+        K[np.ix_(idx, idx)] += 1.0 / h * np.array([[1.0, -1.0], [-1.0, 1.0]])
+    return M, K
+
+
+def _split_fe_reference(prob):
+    """Single-domain Lie splitting written with whole-grid numpy operations: for every
+    step solve (M/dt + S) W = M (U/dt + F) for all columns at once, then shift every
+    row upwind by its Courant number with a periodic roll."""
+    nx, nv, nt, dt = prob.nx, prob.nv, prob.nt, prob.dt
+    M, K = _p1_matrices(nv, prob.hv)
+    A = M / dt + K
+    # Courant number and the column the characteristic comes from (one cell upstream)
+    c = np.abs(prob.v_nodes())[:, None] * dt / prob.hx
+    sgn = np.sign(prob.v_nodes())[:, None]
+    U = prob.u0[:, :nx].copy()
+    levels = [np.concatenate([U, U[:, :1]], axis=1)]
+    for n in range(nt):
+        F = sum(prob.f_time[r, n + 1] * prob.f_space[r][:, :nx] for r in range(prob.f_time.shape[0]))
+        W = np.linalg.solve(A, M @ (U / dt + F))
+        upstream = np.where(sgn > 0, np.roll(W, 1, axis=1), np.where(sgn < 0, np.roll(W, -1, axis=1), W))
+        U = (1.0 - c) * W + c * upstream  # linear interpolation at the foot of the characteristic
+        levels.append(np.concatenate([U, U[:, :1]], axis=1))
+    return np.array(levels)
+
+
+def _fe(prob):
+    return prob.replace(scheme=1, neumann_v=True, periodic_x=True)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_split_fe_matches_whole_grid_numpy(seed):
+    prob = _fe(inputs.random_data(6, 10, 4, 0.05, 1, 0, False, seed=seed, v_range=(-1.0, 1.25)))
+    ref = _split_fe_reference(prob)
+    _, u_all = oracle.monolithic(prob, all_levels=True)
+    np.testing.assert_allclose(u_all, ref, rtol=0, atol=1e-13)
+
+
+def test_split_fe_rejects_other_boundaries():
+    prob = inputs.random_data(6, 10, 4, 0.05, 1, 0, False, seed=0).replace(scheme=1)
+    assert oracle.validate(prob) == -1
+    assert oracle.validate(prob.replace(periodic_x=True, neumann_v=True)) == 0
+
+
+@pytest.mark.parametrize("k", [0, 1, 4])
+@pytest.mark.parametrize("nstrips,robin,overlap", [(1, False, 0), (4, True, 0), (4, True, 3), (4, False, 2)])
+def test_split_fe_cosine_eigen_solution(k, nstrips, robin, overlap):
+    """cos(k pi i / nv) is a generalised eigenvector of the P1 pair with natural ends,
+    S phi = mu M phi, mu = 6 (1 - cos theta) / (h^2 (2 + cos theta)), theta = k pi / nv;
+    one step multiplies it by 1 / (1 + dt mu), and transport leaves x-constant data alone."""
+    nx, nv, nt, dt = 6, 32, 10, 0.004
+    h = 2.0 / nv
+    theta = k * math.pi / nv
+    mu = 6.0 * (1.0 - math.cos(theta)) / (h * h * (2.0 + math.cos(theta)))
+    phi = np.cos(theta * np.arange(nv + 1))
+    u0 = np.repeat(phi[:, None], nx + 1, axis=1)
+    nif = max(nstrips - 1, 0)
+    prob = inputs.Problem(0, 1, -1.0, 1.0, dt, nx, nv, nt, nstrips, overlap, robin, np.full(nif, 5.0),
+                          np.full(nif, 5.0), u0, np.zeros((1, nt + 1)), np.zeros((1, nv + 1, nx + 1)), None,
+                          None, neumann_v=True, periodic_x=True, scheme=1)
+    exact = (1.0 / (1.0 + dt * mu)) ** nt * u0
+    if nstrips == 1:
+        np.testing.assert_allclose(oracle.monolithic(prob), exact, rtol=0, atol=2e-14)
+    else:
+        res = oracle.swr_solve(prob, 400, 1e-13, 0)
+        assert res["iters"] < 400
+        np.testing.assert_allclose(res["u_T"], exact, rtol=0, atol=1e-12)
+
+
+def test_split_fe_conserves_the_p1_mass():
+    """1^T M u summed over the nx unique columns changes by dt * 1^T M f per step."""
+    prob = _fe(inputs.random_data(12, 24, 8, 0.01, 1, 0, False, seed=5, v_range=(-2.0, 2.0)))
+    M, _ = _p1_matrices(prob.nv, prob.hv)
+    ones = np.ones(prob.nv + 1) @ M
+    _, u_all = oracle.monolithic(prob, all_levels=True)
+    mass = np.array([ones @ u[:, : prob.nx].sum(axis=1) for u in u_all])
+    src = np.array([sum(prob.f_time[r, n] * (ones @ prob.f_space[r][:, : prob.nx].sum(axis=1))
+                        for r in range(prob.f_time.shape[0])) for n in range(prob.nt + 1)])
+    np.testing.assert_allclose(np.diff(mass), prob.dt * src[1:], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("robin,overlap", [(False, 2), (True, 0), (True, 2)])
+def test_split_fe_trace_map_fixed_point_is_single_domain(robin, overlap):
+    prob = _fe(inputs.random_data(4, 8, 3, 0.05, 2, overlap, robin, p=3.0, q=5.0, seed=3))
+    M, c = _trace_map(prob)
+    lam_star = np.linalg.solve(np.eye(len(c)) - M, c).reshape(oracle.trace_shape(prob))
+    lam_out, bands, u_T = oracle.swr_iteration(prob, lam_star)
+    np.testing.assert_allclose(u_T, _split_fe_reference(prob)[-1], rtol=0, atol=1e-12)
+    assert np.abs(bands[:, 0] - bands[:, 1]).max() < 1e-12
+
+
+@pytest.mark.parametrize("vbar", [1.0, -1.0])
+def test_split_fe_kolmogorov_gaussian_first_order(vbar):
+    """The splitting (dt for both substeps, Courant number |v| dt / hx) converges at first
+    order to Kolmogorov's closed form, like the unsplit scheme, for a density drifting to
+    the right (vbar = 1) or to the left (vbar = -1)."""
+    errs = []
+    for nx in (100, 200, 400):
+        prob, exact = _gaussian_problem(nx, 800, 0.05, 0.8, vbar=vbar)
+        u = oracle.monolithic(_fe(prob))
+        errs.append(np.abs(u - exact).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert errs[2] < 0.05, errs
+    assert 1.6 < r1 < 2.4 and 1.6 < r2 < 2.4, (errs, r1, r2)
