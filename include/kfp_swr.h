@@ -82,6 +82,14 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
                                   * node 0 in every output; bc_xin, column nx of u0 and f_space, and
                                   * column nx of lambda0 / set_traces data are ignored (replaced by
                                   * column 0); needs nx >= 2 */
+#define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each
+                                  * step (M + dt S) w = M (u^n + dt f^{n+1}) with P1 elements in v
+                                  * (mass M, stiffness S; Robin ends add dt p or dt q to the end row
+                                  * and dt lambda to its right-hand side), then explicit upwind
+                                  * transport u^{n+1} = w - c_i (w - w_upstream), c_i = |v_i| dt / hx;
+                                  * needs KFP_FLAG_NEUMANN_V | KFP_FLAG_PERIODIC_X.  The interface data
+                                  * come from w: Dirichlet w, Robin without overlap (p+q) w - lambda_in,
+                                  * Robin with overlap p w (q w) minus the half-row residual */
 
 typedef struct {
   double x0, x1, v0, v1; /* box [x0,x1] x [v0,v1], x1 > x0, v1 > v0 */

@@ -1,0 +1,177 @@
+// kfp_fe.cuh -- sweep pass of the Lie splitting of Section 6.2 (sm_103a).
+//
+// One time step of the paper's own scheme for the model problem (periodic in x,
+// zero flux in v):
+//   step 1  (M + dt S) w = M z,  z = u^n + dt f^{n+1}     (P1 elements in v, implicit
+//           Euler over dt; both sides scaled by dt), per x-column; a Robin end adds
+//           dt p (top) or dt q (bottom) to the end row and dt lambda to its right-hand
+//           side, a Dirichlet end sets w = lambda;
+//   step 2  u^{n+1} = w - c_i (w - w_upstream), c_i = |v_i| dt / hx  (upwind transport).
+// As in the unsplit sweep, one launch per time step fuses the back-substitution of
+// step k (it produces w^k row by row) with the elimination of step k+1; lanes are
+// x-columns and the upstream value of a row comes from a warp shuffle.  Two
+// differences: the transport now follows the solve (u^k = T w^k), and the
+// right-hand side M z of a row needs z of both neighbouring rows, so the
+// elimination runs one row behind the back-substitution.
+//
+// Outgoing interface data come from w^k: Dirichlet w; Robin without overlap
+// (p + q) w - lambda_in; Robin with overlap p w (q w) minus the half-row residual of
+// this strip at the node, which needs z^k of the node and its neighbour: those two
+// values per end are kept from the previous pass in a small buffer Zrec.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kfp_kernels.cuh"
+
+namespace kfp {
+
+struct FeArgs {
+  double m_full, m_half, m_off;  // P1 mass matrix entries: 2h/3, h/3 (end node), h/6
+  double k_half, k_off;          // (M + dt S) entries of an end row: h/3 + dt/h, h/6 - dt/h
+  double dt, inv_dt;
+  double* zrec;                  // [2 parities][S][2 ends][2 rows][nx+1] z^k at the trace rows
+};
+
+template <typename T, bool UP, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (w >= A.W) return;  // whole warp leaves together
+  const int s = blockIdx.y + A.strip0;
+  const StripInfo st = A.strips[s];
+  const int m = w * kOutCols - 1 + lane;
+  const int col = m + 1;
+  const bool in_dom = (m >= 0) && (m <= A.nx);
+  const bool out_lane = in_dom && lane >= 1 && lane <= kOutCols;
+  const int L = st.L, lo = st.lo, P = A.P, nxp = A.nx + 1, nt = A.nt;
+  const int dirE = UP ? 0 : 1;
+  const int dirB = UP ? 1 : 0;
+  // periodic x: every column has the same factors (class 1)
+  const T* __restrict__ gE = A.coef + ((size_t)((s * 3 + 1) * 2 + dirE) * 3 + 0) * A.Lmax;
+  const T* __restrict__ aE = A.coef + ((size_t)((s * 3 + 1) * 2 + dirE) * 3 + 1) * A.Lmax;
+  const T* __restrict__ cpB = A.coef + ((size_t)((s * 3 + 1) * 2 + dirB) * 3 + 2) * A.Lmax;
+  const T* __restrict__ Ycur = (k & 1) ? A.Y1 : A.Y0;
+  T* __restrict__ Ynext = ((k + 1) & 1) ? A.Y1 : A.Y0;
+  const int k1 = k + 1;
+  const int ov = A.ov;
+  const bool robin_ov = A.robin && ov >= 1;
+  const size_t zslab = (size_t)2 * 2 * nxp;  // one strip's Zrec entries
+  const double* zcur = E.zrec + ((size_t)(k & 1) * A.S + s) * zslab;
+  double* znext = E.zrec + ((size_t)(k1 & 1) * A.S + s) * zslab;
+
+  // local rows of the outgoing data: top = alpha_s (data for the strip above),
+  // bottom = beta_{s-1} (data for the strip below); the half-row residual of the top
+  // node uses the row below it, that of the bottom node the row above it
+  const int aT = st.has_top ? st.alpha_top - lo : -10;
+  const int bB = st.has_bot ? st.alpha_bot - lo + ov : -10;
+  const int aB = st.alpha_bot - lo;
+
+  // interface data of this strip for the system being eliminated (t^{k+1})
+  double lam_rhs_top = 0.0, lam_rhs_bot = 0.0;
+  if (MODE != 2 && in_dom) {
+    if (st.has_top) lam_rhs_top = A.lam_in[(((size_t)s * 2 + 0) * nt + k) * nxp + m];
+    if (st.has_bot) lam_rhs_bot = A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + k) * nxp + m];
+  }
+
+  T w_prev = T(0), y_prev = T(0), zm1 = T(0), zm2 = T(0);
+  // elimination of local row l from the M-weighted right-hand side rhs
+  auto eliminate = [&](int l, T rhs) {
+    const bool top_end = l == L - 1, bot_end = l == 0;
+    T R = rhs;
+    if (top_end && st.has_top) R = A.robin ? (T)((double)R + E.dt * lam_rhs_top) : (T)lam_rhs_top;
+    if (bot_end && st.has_bot) R = A.robin ? (T)((double)R + E.dt * lam_rhs_bot) : (T)lam_rhs_bot;
+    const T y = gE[l] * (R - aE[l] * y_prev);
+    if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
+    y_prev = y;
+  };
+
+  for (int t = 0; t < L; ++t) {
+    const int l = UP ? t : (L - 1 - t);
+    const int i = lo + l;
+    T u;
+    if (MODE == 0) {
+      u = A.U0[(size_t)i * P + col];
+    } else {
+      const T wv = Ycur[(size_t)(st.rowoff + l) * P + col] - cpB[l] * w_prev;
+      const T wlast = w_prev;  // w of the previous row in pass order
+      w_prev = wv;
+      // ---- outgoing interface data of t^k from w^k ----
+      if (out_lane) {
+        if (st.has_top) {
+          const int eT = robin_ov ? (UP ? aT : aT - 1) : aT;  // the later of alpha, alpha-1
+          if (l == eT) {
+            const double wa = robin_ov && !UP ? (double)wlast : (double)wv;  // w(alpha)
+            double lam;
+            if (!A.robin) {
+              lam = wa;
+            } else if (ov >= 1) {
+              const double wb = UP ? (double)wlast : (double)wv;  // w(alpha - 1)
+              const double* zk = zcur + 0 * 2 * nxp;               // z^k at alpha, alpha-1
+              lam = st.q_top * wa - E.inv_dt * (E.k_half * wa + E.k_off * wb - E.m_half * zk[m] - E.m_off * zk[nxp + m]);
+            } else {
+              lam = (st.p_top + st.q_top) * wa - A.lam_in[(((size_t)s * 2 + 0) * nt + (k - 1)) * nxp + m];
+            }
+            A.lam_next[(((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m] = lam;
+          }
+        }
+        if (st.has_bot) {
+          const int eB = robin_ov ? (UP ? bB + 1 : bB) : bB;  // the later of beta, beta+1
+          if (l == eB) {
+            const double wbeta = robin_ov && UP ? (double)wlast : (double)wv;  // w(beta)
+            double lam;
+            if (!A.robin) {
+              lam = wbeta;
+            } else if (ov >= 1) {
+              const double wu = UP ? (double)wv : (double)wlast;  // w(beta + 1)
+              const double* zk = zcur + 1 * 2 * nxp;              // z^k at beta, beta+1
+              lam = st.p_bot * wbeta - E.inv_dt * (E.k_half * wbeta + E.k_off * wu - E.m_half * zk[m] - E.m_off * zk[nxp + m]);
+            } else {
+              lam = (st.p_bot + st.q_bot) * wbeta -
+                    A.lam_bot_src[((((size_t)s - 1) * 2 + 1) * nt + (k - 1)) * nxp + m];
+            }
+            A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
+          }
+        }
+      }
+      // ---- transport over dt: u^k = w^k - c (w^k - w^k upstream) ----
+      const T wnb = shfl_val(wv, lane - A.sgn[i]);
+      u = wv - A.cabs[i] * (wv - wnb);
+      // ---- overlap values of u^k ----
+      if (out_lane) {
+        if (st.has_top && l >= aT && l <= aT + ov)
+          A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)u;
+        if (st.has_bot && l >= aB && l <= aB + ov)
+          A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)u;
+      }
+      if (MODE == 2) {
+        if (out_lane) A.UT[(size_t)(st.rowoff + l) * P + col] = u;
+        continue;
+      }
+    }
+    // ---- z^{k+1} = u^k + dt f^{k+1}; keep it at the trace rows for the next pass ----
+    T z = u;
+    for (int r = 0; r < A.nforce; ++r)
+      z += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
+    if (robin_ov && out_lane) {  // halo lanes hold a wrong u (their upstream lane is missing)
+      if (st.has_top && (l == aT || l == aT - 1)) znext[(size_t)(0 * 2 + (aT - l)) * nxp + m] = (double)z;
+      if (st.has_bot && (l == bB || l == bB + 1)) znext[(size_t)(1 * 2 + (l - bB)) * nxp + m] = (double)z;
+    }
+    // ---- eliminate the previous row in pass order, whose right-hand side is now known ----
+    if (t >= 1) {
+      const int lp = UP ? t - 1 : L - t;
+      const T rhs = (t == 1) ? (T)(E.m_half * (double)zm1 + E.m_off * (double)z)  // end row: one element
+                             : (T)(E.m_off * (double)zm2 + E.m_full * (double)zm1 + E.m_off * (double)z);
+      eliminate(lp, rhs);
+    }
+    zm2 = zm1;
+    zm1 = z;
+  }
+  if (MODE != 2) {
+    // the last row in pass order: an end row (one element)
+    const T rhs = (L == 1) ? (T)(E.m_half * (double)zm1) : (T)(E.m_half * (double)zm1 + E.m_off * (double)zm2);
+    eliminate(UP ? L - 1 : 0, rhs);
+  }
+}
+
+}  // namespace kfp

@@ -11,6 +11,7 @@
 #include "kfp_kernels.cuh"
 #include "kfp_sweep_tma.cuh"
 #include "kfp_adjoint.cuh"
+#include "kfp_fe.cuh"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -46,6 +47,7 @@ struct Geometry {
   double x0, x1, v0, v1, dt, hx, hv, r;
   int nx, nv, nt, S, ov, robin, P, W, Lmax, rows, nforce;
   int neumann, periodic;  // zero flux in v, periodic in x (Section 6.1)
+  int split;              // the Lie splitting with P1 elements of Section 6.2
   std::vector<double> p, q;
   std::vector<kfp::StripInfo> strips;
   std::vector<int> row_of;  // [nv+1] row of UT holding node i at t = T
@@ -93,6 +95,9 @@ kfp_status build_geometry(const kfp_swr_desc* d, int nforce, Geometry* g, std::s
   g->neumann = (d->flags & KFP_FLAG_NEUMANN_V) ? 1 : 0;
   g->periodic = (d->flags & KFP_FLAG_PERIODIC_X) ? 1 : 0;
   if (g->periodic && d->nx < 2) return bad(KFP_EINVAL, "periodic x needs nx >= 2");
+  g->split = (d->flags & KFP_FLAG_SPLIT_SCHEME) ? 1 : 0;
+  if (g->split && !(g->neumann && g->periodic))
+    return bad(KFP_EINVAL, "the split scheme is built for the model problem: zero flux in v, periodic x");
   g->hx = (d->x1 - d->x0) / d->nx;
   g->hv = (d->v1 - d->v0) / d->nv;
   g->r = d->dt / (g->hv * g->hv);
@@ -135,6 +140,28 @@ kfp_status build_geometry(const kfp_swr_desc* d, int nforce, Geometry* g, std::s
   return KFP_OK;
 }
 
+// Rows of the split scheme's system (M + dt S) w (Section 6.2, P1 elements in v):
+// interior (h/6 - dt/h, 2h/3 + 2dt/h, h/6 - dt/h); an end row (strip end or v0, v1)
+// has one element, h/3 + dt/h on the diagonal, plus dt p (top) or dt q (bottom) at a
+// Robin interface; a Dirichlet interface row is the identity.
+void split_rows(const Geometry& g, const kfp::StripInfo& st, double* a, double* b, double* c) {
+  const double h = g.hv, dt = g.dt;
+  for (int l = 0; l < st.L; ++l) {
+    const bool top = l == st.L - 1, bot = l == 0;
+    a[l] = bot ? 0.0 : h / 6 - dt / h;
+    c[l] = top ? 0.0 : h / 6 - dt / h;
+    b[l] = (top || bot) ? h / 3 + dt / h : 2 * h / 3 + 2 * dt / h;
+    if (top && st.has_top) {
+      if (g.robin) b[l] += dt * st.p_top;
+      else { a[l] = 0.0; b[l] = 1.0; }
+    }
+    if (bot && st.has_bot) {
+      if (g.robin) b[l] += dt * st.q_bot;
+      else { c[l] = 0.0; b[l] = 1.0; }
+    }
+  }
+}
+
 // Constant-coefficient LU factors of every strip's implicit-Euler system for the
 // three column classes (m = 0, interior, m = nx) and both elimination directions.
 // Layout [S][3][2][3][Lmax]: field 0 = 1/pivot, 1 = coupling to the previously
@@ -147,7 +174,8 @@ std::vector<double> build_factors(const Geometry& g) {
     const kfp::StripInfo& st = g.strips[s];
     const int L = st.L;
     for (int kappa = 0; kappa < 3; ++kappa) {
-      for (int l = 0; l < L; ++l) {
+      if (g.split) split_rows(g, st, a.data(), b.data(), c.data());
+      for (int l = 0; l < L && !g.split; ++l) {
         const int i = st.lo + l;
         const double vi = g.v0 + i * g.hv;
         const bool inflow = !g.periodic && ((kappa == 0 && vi > 0) || (kappa == 2 && vi < 0));
@@ -227,6 +255,7 @@ struct kfp_swr {
   double* lam_in = nullptr;
   double* lam_next = nullptr;
   double* bands = nullptr;
+  double* zrec = nullptr;      // split scheme: z^k at the trace rows, [2][S][2][2][nx+1]
   double* partial = nullptr;   // 2 doubles per reduction block
   unsigned* tickets = nullptr; // [2]
   double* scal = nullptr;      // [3] e_mis, e_chg, j_l2
@@ -326,6 +355,22 @@ struct kfp_swr {
     const int groups = serial ? g.S : 1;
     const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
     const dim3 block(kfp::kWarpsPerBlock * 32);
+    if (g.split) {
+      const kfp::FeArgs E = fe_args();
+      for (int grp = 0; grp < groups; ++grp) {
+        A.strip0 = serial ? grp : 0;
+        kfp::fe_pass_kernel<T, true, 0><<<grid, block, 0, st>>>(A, E, 0);
+        wrap_after_pass<T>(st, 0, A.strip0, serial ? 1 : g.S);
+        for (int k = 1; k < g.nt; ++k) {
+          if (k & 1) kfp::fe_pass_kernel<T, false, 1><<<grid, block, 0, st>>>(A, E, k);
+          else       kfp::fe_pass_kernel<T, true, 1><<<grid, block, 0, st>>>(A, E, k);
+          wrap_after_pass<T>(st, k, A.strip0, serial ? 1 : g.S);
+        }
+        if (g.nt & 1) kfp::fe_pass_kernel<T, false, 2><<<grid, block, 0, st>>>(A, E, g.nt);
+        else          kfp::fe_pass_kernel<T, true, 2><<<grid, block, 0, st>>>(A, E, g.nt);
+      }
+      return;
+    }
     for (int grp = 0; grp < groups; ++grp) {
       A.strip0 = serial ? grp : 0;
       // pass k runs in ascending row order when k is even (step 1 is factored upward)
@@ -350,6 +395,20 @@ struct kfp_swr {
     const int r0 = g.strips[s0].rowoff;
     const int r1 = (s0 + ns < g.S) ? g.strips[s0 + ns].rowoff : g.rows;
     kfp::periodic_wrap_kernel<T><<<(r1 - r0 + 255) / 256, 256, 0, st>>>(Yn + (size_t)r0 * g.P, r1 - r0, g.P, g.nx);
+  }
+
+  kfp::FeArgs fe_args() const {
+    kfp::FeArgs E;
+    const double h = g.hv;
+    E.m_full = 2.0 * h / 3.0;
+    E.m_half = h / 3.0;
+    E.m_off = h / 6.0;
+    E.k_half = h / 3.0 + g.dt / h;
+    E.k_off = h / 6.0 - g.dt / h;
+    E.dt = g.dt;
+    E.inv_dt = 1.0 / g.dt;
+    E.zrec = zrec;
+    return E;
   }
 
   template <typename T>
@@ -669,7 +728,7 @@ struct kfp_swr {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
-                    lam_in, lam_next, bands, partial, tickets, scal, hist, iter, stage, d_res,
+                    lam_in, lam_next, bands, zrec, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_scratch, adj_fac, adj_grad};
     for (void* b : bufs)
       if (b) cudaFree(b);
@@ -983,7 +1042,11 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   }
 
   // TMA-fed sweep: records, pre-scaled forcing, tensor maps
-  if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
+  if (g.split) {
+    const size_t nz = (size_t)2 * g.S * 2 * 2 * nxp;
+    TRY(alloc(h, (void**)&h->zrec, sizeof(double) * nz));
+    cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream);
+  } else if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
     rc = setup_tma(h, pb);
     if (rc) return rc;
   }
@@ -1121,7 +1184,7 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
                          double* grad_q) {
   Geometry& g = h->g;
   if (!g.robin || g.ov != 0 || g.S < 2 || h->prec != KFP_F64 || h->inner || (h->flags & KFP_FLAG_GAUSS_SEIDEL) ||
-      g.neumann || g.periodic)
+      g.neumann || g.periodic || g.split)
     return h->fail(KFP_ENOTSUP,
                    "the adjoint needs FP64, Robin transmission, no overlap, >= 2 strips and the parallel form");
   if (K < 1) return h->fail(KFP_EINVAL, "need K >= 1");
@@ -1683,7 +1746,7 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
       rc = KFP_ENOTSUP;
       break;
     }
-    if (descs[i].flags & (KFP_FLAG_NEUMANN_V | KFP_FLAG_PERIODIC_X)) {
+    if (descs[i].flags & (KFP_FLAG_NEUMANN_V | KFP_FLAG_PERIODIC_X | KFP_FLAG_SPLIT_SCHEME)) {
       g_batch_create_error = "the batched sweep takes Dirichlet data in x and v only";
       rc = KFP_ENOTSUP;
       break;

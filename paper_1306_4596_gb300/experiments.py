@@ -11,7 +11,9 @@
 
 Every run solves the error equation of the model problem (Section 6.1: periodic in
 x, zero flux in v, f = 0, u0 = 0, T = 2) on two strips split at v = 0 from a random
-lambda_1^0, in the serial order SWR1-SWR4 of Section 6.3 unless ``parallel`` is set.
+lambda_1^0, in the serial order SWR1-SWR4 of Section 6.3 unless ``parallel`` is set,
+with the implicit-Euler/upwind scheme or (``scheme=1``) the paper's own Lie splitting
+with P1 elements of Section 6.2.
 The exact solution of the error equation is zero, so besides the stopping norm each
 run reports the true error max |u^k(T)|: the classical algorithm without overlap
 stops at once in the serial order (both strips take the same interface value, so
@@ -46,9 +48,10 @@ METHODS = {
 }
 
 
-def _problem(j: int, overlap: int, robin: bool, p: float, q: Optional[float], parallel: bool, seed: int):
+def _problem(j: int, overlap: int, robin: bool, p: float, q: Optional[float], parallel: bool, seed: int,
+             scheme: int = 0):
     prob = inputs.model_error_equation(j, overlap=overlap, robin=robin, p=p, q=q, seed=seed)
-    return prob.replace(gauss_seidel=not parallel)
+    return prob.replace(gauss_seidel=not parallel, scheme=scheme)
 
 
 def count_iterations(prob, max_iters: int = MAX_ITERS, tol: float = TOL, precision: str = "f64") -> Dict:
@@ -67,20 +70,21 @@ def count_iterations(prob, max_iters: int = MAX_ITERS, tol: float = TOL, precisi
 
 def table1(levels: Iterable[int] = (0, 1, 2, 3, 4), parallel: bool = False, seed: int = 7,
            max_iters: int = MAX_ITERS, precision: str = "f64", methods: Optional[List[str]] = None,
-           log=None) -> List[Dict]:
+           log=None, scheme: int = 0) -> List[Dict]:
     rows = []
     for overlap in (3, 0):
         for name in (methods or list(METHODS)):
             robin, p, q = METHODS[name]
             for j in levels:
-                prob = _problem(j, overlap, robin, p, q, parallel, seed)
+                prob = _problem(j, overlap, robin, p, q, parallel, seed, scheme)
                 # without overlap the classical algorithm cannot converge (Section 6.5):
                 # a few iterations show it
                 cap = min(max_iters, 10) if (overlap == 0 and not robin) else max_iters
                 r = count_iterations(prob, cap, precision=precision)
                 r.pop("history")
                 r.update({"method": name, "overlap": overlap, "j": j, "nx": prob.nx, "nv": prob.nv,
-                          "nt": prob.nt, "order": "parallel" if parallel else "serial"})
+                          "nt": prob.nt, "order": "parallel" if parallel else "serial",
+                          "scheme": "split P1" if scheme == 1 else "implicit Euler + upwind"})
                 rows.append(r)
                 if log:
                     log(json.dumps(r))
@@ -110,11 +114,12 @@ def format_table1(rows: List[Dict], max_iters: int = MAX_ITERS) -> str:
 
 
 def p_scan(ps: Iterable[float], j: int = 0, overlap: int = 3, q: Optional[float] = None, parallel: bool = False,
-           seed: int = 7, max_iters: int = MAX_ITERS, after: int = 15, precision: str = "f64") -> List[Dict]:
+           seed: int = 7, max_iters: int = MAX_ITERS, after: int = 15, precision: str = "f64",
+           scheme: int = 0) -> List[Dict]:
     """Iterations to e_mis < 1e-6 and e_mis after ``after`` iterations for every p
     (q = p unless given).  One solver; the Robin factors are rebuilt in place per p."""
     ps = [float(p) for p in ps]
-    prob = _problem(j, overlap, True, ps[0], q, parallel, seed)
+    prob = _problem(j, overlap, True, ps[0], q, parallel, seed, scheme)
     lam0 = prob.lam0
     out = []
     with _swr.SWR(prob, precision) as s:
@@ -162,17 +167,20 @@ def main(argv=None) -> int:
         sp.add_argument("--parallel", action="store_true", help="parallel form instead of the serial order")
         sp.add_argument("--seed", type=int, default=7)
         sp.add_argument("--precision", default="f64", choices=["f64", "f32"])
+        sp.add_argument("--scheme", type=int, default=0, choices=[0, 1],
+                        help="0: implicit Euler + upwind; 1: the Lie splitting with P1 elements")
     a = ap.parse_args(argv)
     if a.cmd == "table1":
         rows = table1(a.levels, a.parallel, a.seed, a.max_iters, a.precision, a.methods,
-                      log=lambda s: print(s, flush=True))
+                      log=lambda s: print(s, flush=True), scheme=a.scheme)
         print(format_table1(rows, a.max_iters))
     elif a.cmd == "pscan":
-        for r in p_scan(_range(a.p), a.j, a.overlap, None, a.parallel, a.seed, precision=a.precision):
+        for r in p_scan(_range(a.p), a.j, a.overlap, None, a.parallel, a.seed, precision=a.precision,
+                        scheme=a.scheme):
             print(json.dumps(r), flush=True)
     else:
         for r in pq_scan(_range(a.p), _range(a.q), j=a.j, overlap=a.overlap, parallel=a.parallel, seed=a.seed,
-                         precision=a.precision):
+                         precision=a.precision, scheme=a.scheme):
             print(json.dumps(r), flush=True)
     return 0
 

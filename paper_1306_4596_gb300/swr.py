@@ -24,14 +24,15 @@ KFP_DIRICHLET, KFP_ROBIN = 0, 1
 KFP_F64, KFP_F32, KFP_MIXED = 0, 1, 2
 PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
 KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1, 2, 4, 8
-KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X = 16, 32
+KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME = 16, 32, 64
 
 
 def problem_flags(prob) -> int:
     """Flags that a problem's own definition sets: iteration order and boundary conditions."""
     return ((KFP_FLAG_GAUSS_SEIDEL if getattr(prob, "gauss_seidel", False) else 0)
             | (KFP_FLAG_NEUMANN_V if getattr(prob, "neumann_v", False) else 0)
-            | (KFP_FLAG_PERIODIC_X if getattr(prob, "periodic_x", False) else 0))
+            | (KFP_FLAG_PERIODIC_X if getattr(prob, "periodic_x", False) else 0)
+            | (KFP_FLAG_SPLIT_SCHEME if getattr(prob, "scheme", 0) == 1 else 0))
 
 EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces", "kfp_swr_error",
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",

@@ -42,3 +42,14 @@ def test_p_scan_reuses_one_solver():
         fresh = ex.count_iterations(ex._problem(0, 3, True, p, None, parallel=False, seed=7))
         assert row["iters"] == fresh["iters"], (p, row, fresh["iters"])
         assert row["converged"]
+
+
+@pytest.mark.parametrize("method,overlap", [("OSWR(p)", 3), ("OSWR(p,q)", 0)])
+def test_table1_level0_split_scheme_matches_oracle(method, overlap):
+    from paper_1306_4596_gb300 import experiments as ex
+    robin, p, q = ex.METHODS[method]
+    prob = ex._problem(0, overlap, robin, p, q, parallel=False, seed=7, scheme=1)
+    gpu = ex.count_iterations(prob)
+    ref = oracle.swr_solve(prob, ex.MAX_ITERS, ex.TOL, 1)
+    assert gpu["iters"] == ref["iters"], (gpu["iters"], ref["iters"])
+    np.testing.assert_allclose(gpu["history"], ref["hist"][:, 0], rtol=1e-9, atol=1e-12)

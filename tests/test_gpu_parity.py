@@ -110,6 +110,16 @@ SMALL_CASES = [
                                        boundary_data=False), 3),
     ("fast_const_forcing_S3", lambda: RD(120, 300, 4, 0.002, 3, 4, True, p=5.0, seed=23, nforce=1,
                                          constant_in_time=True, boundary_data=False), 3),
+    # strips whose row count is a multiple of 16 (the last chunk is full and holds an end
+    # row) and strips of exactly one chunk (both end rows in it)
+    ("fast_full_last_chunk_robin", lambda: RD(90, 250, 6, 0.002, 2, 3, True, p=4.0, seed=24, nforce=1,
+                                              boundary_data=False), 3),
+    ("fast_full_last_chunk_dirichlet", lambda: RD(90, 250, 6, 0.002, 2, 3, False, seed=25, nforce=1,
+                                                  boundary_data=False), 3),
+    ("fast_one_chunk_strips_robin", lambda: RD(70, 60, 5, 0.004, 4, 0, True, p=3.0, q=2.0, seed=26, nforce=1,
+                                               boundary_data=False), 3),
+    ("fast_one_chunk_strips_dirichlet", lambda: RD(70, 60, 5, 0.004, 4, 0, False, seed=27, nforce=0,
+                                                   boundary_data=False), 3),
     ("bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=11), 2),
     ("bumps_dirichlet_ov4", lambda: inputs.gaussian_bumps(130, 256, 30, 1.5e-3, 4, seed=12, overlap=4,
                                                           robin=False), 2),
@@ -318,3 +328,42 @@ def test_model_problem_conserves_mass_on_gpu():
         u_T = s.solution()
     m0 = mass(prob.u0)
     assert abs(mass(u_T) - m0) <= 1e-11 * abs(m0)
+
+
+# The paper's own scheme (Section 6.2): Lie splitting with P1 elements in v, on the
+# model problem (zero flux in v, periodic x).
+SPLIT_CASES = [
+    ("split_robin_S4_ov0", lambda: RD(61, 64, 5, 0.005, 4, 0, True, p=3.0, q=1.5, seed=70, nforce=1), 3),
+    ("split_robin_S2_ov3", lambda: RD(89, 96, 6, 0.004, 2, 3, True, p=4.0, seed=71, nforce=2), 3),
+    ("split_dirichlet_S3_ov2", lambda: RD(30, 48, 5, 0.005, 3, 2, False, seed=72, nforce=0), 3),
+    ("split_robin_S4_ov1_pq", lambda: RD(119, 128, 4, 0.003, 4, 1, True, p=5.0, q=2.0, seed=73, nforce=1), 3),
+    ("split_single_strip", lambda: RD(29, 32, 6, 0.01, 1, 0, False, seed=74, nforce=1), 1),
+    ("split_bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=75), 2),
+]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,iters", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_split_scheme_matches_oracle(label, factory, iters, precision):
+    prob = factory().replace(neumann_v=True, periodic_x=True, scheme=1)
+    ref = run_oracle(prob, iters)
+    gpu = run_gpu(prob, iters, precision)
+    (check_f64 if precision == "f64" else check_f32)(gpu, ref, prob)
+    assert np.array_equal(gpu["u_T"][:, prob.nx], gpu["u_T"][:, 0])
+
+
+def test_split_scheme_serial_order():
+    prob = RD(89, 96, 6, 0.004, 3, 3, True, p=4.0, seed=76, nforce=1).replace(
+        neumann_v=True, periodic_x=True, scheme=1, gauss_seidel=True)
+    check_f64(run_gpu(prob, 3), run_oracle(prob, 3), prob)
+
+
+def test_split_scheme_converges_to_single_domain():
+    prob = inputs.gaussian_bumps(120, 256, 30, 1.5e-3, 4, p=4.0, seed=77, overlap=2).replace(
+        neumann_v=True, periodic_x=True, scheme=1)
+    mono = oracle.monolithic(prob)
+    swr = _swr()
+    with swr.SWR(prob, "f64") as s:
+        s.sweep(300, tol=1e-13)
+        u = s.solution()
+    assert np.abs(u - mono).max() <= 1e-11 * np.abs(mono).max()
