@@ -13,7 +13,8 @@ timed region; the state of one step (3 x 68 MB) is larger than L2 (129 MB).
 Extra keys: "roofline" (sweep kernel: FP64 is bound by the FP64 pipe, FP32 by HBM),
 "cpu_baseline" (the CPU oracle on a bounded sample), "e2e" (through the C ABI from
 pinned host buffers, copies included), "clocks" (nvidia-smi during the timed
-region), "variants" (the FP32 form), "time_to_tol" (wall time to e_mis < 1e-8 for
+region), "variants" (the FP32 form; the model problem's periodic x and zero-flux v with
+this library's scheme and with the paper's split P1 scheme), "time_to_tol" (wall time to e_mis < 1e-8 for
 the plain FP64 form and the mixed-precision form) and "batched" (256 uneven seeded
 problems swept together, FP64 and FP32, autotuned launch shape) and "adjoint" (time of
 one gradient of the interface mismatch after 10 iterations, and 20 Adam steps on the
@@ -338,6 +339,18 @@ def main():
             var["hbm_gbs"] = cells_per_pass * BYTES_PER_CELL["f32"] / (avg2 / 1e3) / 1e9
             var["hbm_frac"] = var["hbm_gbs"] / hbm
         line["variants"] = [var]
+        # the paper's model-problem boundaries (periodic x, zero flux in v) on the same
+        # grid: with this library's scheme and with the split P1 scheme of Section 6.2
+        for label, kw in (("periodic x, zero flux v", {}), ("split P1 scheme (Section 6.2), periodic x, zero flux v",
+                                                           {"scheme": 1})):
+            mprob = prob.replace(neumann_v=True, periodic_x=True, **kw)
+            with swr_mod.SWR(mprob, args.precision, inputs_on="device", profile=True) as s:
+                n3 = 2
+                ms3, _ = time_iterations(torch, s, n3, 1, None, 1, device_index)
+                st3 = s.stats()
+            line["variants"].append({"dtype": args.precision, "boundaries": label,
+                                     "value": cells_per_iter * n3 / (ms3 / 1e3), "unit": UNIT,
+                                     "avg_pass_ms": st3["sweep_ms"] / st3["iterations"] / pass_launches})
 
         # ---- time to e_mis < 1e-8: plain FP64 vs mixed precision ----------------------
         ttol = {}
