@@ -15,9 +15,6 @@
 // outgoing data).  Backward over iterations, the lambda_in_bar of iterate k is the
 // lambda_out_bar of iterate k-1 (same slots).  Only interface-node values of the
 // forward iterates enter, so no forward state is stored or recomputed.
-//
-// One thread owns one (strip, column) and solves its transposed tridiagonal system
-// with host-factored coefficients; the elimination residue goes to a scratch array.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -25,112 +22,156 @@
 
 namespace kfp {
 
-struct AdjArgs {
-  int nx, nv, nt, S, Lmax;
+// ---------------------------------------------------------------------------
+// One launch per time level, lanes = x-columns.
+//
+// The adjoint of one iterate runs the forward schedule backward: pass j
+// back-substitutes level nt-j+1 (its system was eliminated by pass j-1 in the other
+// row order) and, in the same row order, eliminates level nt-j.  The transposed
+// upwind term E^T w^{l+1} of a row needs w^{l+1} of the downstream column, which
+// comes from a warp shuffle (lane + sign of v); lanes 0 and 31 are halo columns
+// that recompute their neighbour's back-substitution, as in the forward sweep.
+// Only the elimination residue is stored (Y[2][rows][P], column m at m+1).
+// ---------------------------------------------------------------------------
+
+struct AdjPassArgs {
+  int nx, nv, nt, P, W, Lmax;
   double two_dt_hv, dthx;
   const StripInfo* strips;
-  const double* fac;        // [S][3 classes][3 fields][Lmax]: 1/pivot, sub-diagonal, back-substitution coef
+  const double* coef;       // [S][3][2][3][Lmax] LU of A^T per class and direction: 1/pivot, coupling, cp
   const double* cabs;       // [nv+1] |v_i| dt / hx
   const signed char* sgn;   // [nv+1]
   const double* bands;      // [S-1][2][nt][nx+1] interface-node values of this iterate
-  const double* lbar_out;   // [S-1][2][nt][nx+1] adjoint of the data this iterate produced
-  double* lbar_in;          // same layout: adjoint of the data this iterate consumed
-  double* contrib;          // [S-1][4][nt][nx+1]: dJ/dp from the lower strip, dJ/dq from the lower strip,
-                            //                      dJ/dp from the upper strip, dJ/dq from the upper strip
-  double* w0;               // [rows][nx+1] adjoint state, even levels
-  double* w1;               // odd levels
-  double* scratch;          // [rows][nx+1] elimination residue
-  int rows;
+  const double* lbar_out;   // [S-1][2][nt][nx+1]
+  double* lbar_in;
+  double* contrib;          // [S-1][4][nt][nx+1]
+  double* Y0;               // [rows][P] elimination residue, even passes
+  double* Y1;               // odd passes
 };
 
-// Row type at node i, column m of strip s: 0 interior, 1 identity, 2 Robin top, 3 Robin bottom.
-__device__ __forceinline__ int adj_row_kind(const AdjArgs& A, const StripInfo& st, int i, int m) {
-  if (i == 0 || i == A.nv) return 1;
-  const int sg = A.sgn[i];
-  if ((m == 0 && sg > 0) || (m == A.nx && sg < 0)) return 1;
-  if (st.has_top && i == st.hi) return 2;
-  if (st.has_bot && i == st.lo) return 3;
-  return 0;
+// row (i, m) of the forward system is an identity row (v boundary or x inflow);
+// sg = sign of v_i
+__device__ __forceinline__ bool adj_identity(const AdjPassArgs& A, int i, int m, int sg) {
+  if (i == 0 || i == A.nv) return true;
+  return (m == 0 && sg > 0) || (m == A.nx && sg < 0);
 }
 
-// Level l (1..nt) of the adjoint of one iterate, all strips and columns.
-__global__ void __launch_bounds__(128)
-adjoint_level_kernel(const AdjArgs A, const int l, const int last_iterate) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// MODE 0: eliminate level nt (no back-substitution); 1: back-substitute level
+// nt-j+1 and eliminate level nt-j; 2: back-substitute level 1 only.
+template <bool UP, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (w >= A.W) return;  // whole warp leaves together
   const int s = blockIdx.y;
-  if (m > A.nx) return;
   const StripInfo st = A.strips[s];
-  const int L = st.L, lo = st.lo, nxp = A.nx + 1, nt = A.nt;
-  const int cls = m == 0 ? 0 : (m == A.nx ? 2 : 1);
-  const double* g = A.fac + ((size_t)(s * 3 + cls) * 3 + 0) * A.Lmax;
-  const double* sub = A.fac + ((size_t)(s * 3 + cls) * 3 + 1) * A.Lmax;
-  const double* cp = A.fac + ((size_t)(s * 3 + cls) * 3 + 2) * A.Lmax;
-  const double* wn = (l + 1) & 1 ? A.w1 : A.w0;  // w^{l+1} (zero beyond nt)
-  double* wc = l & 1 ? A.w1 : A.w0;               // w^l
-  const bool have_next = l < nt;
+  const int m = w * kOutCols - 1 + lane;
+  const int col = m + 1;
+  const bool in_dom = (m >= 0) && (m <= A.nx);
+  const bool out_lane = in_dom && lane >= 1 && lane <= kOutCols;
+  const int cls = (m <= 0) ? 0 : (m >= A.nx ? 2 : 1);
+  const int L = st.L, lo = st.lo, P = A.P, nxp = A.nx + 1, nt = A.nt;
+  const int dirE = UP ? 0 : 1, dirB = UP ? 1 : 0;
+  const double* __restrict__ gE = A.coef + ((size_t)((s * 3 + cls) * 2 + dirE) * 3 + 0) * A.Lmax;
+  const double* __restrict__ aE = A.coef + ((size_t)((s * 3 + cls) * 2 + dirE) * 3 + 1) * A.Lmax;
+  const double* __restrict__ cpB = A.coef + ((size_t)((s * 3 + cls) * 2 + dirB) * 3 + 2) * A.Lmax;
+  const double* __restrict__ Ycur = (j & 1) ? A.Y0 : A.Y1;   // written by pass j-1
+  double* __restrict__ Ynext = (j & 1) ? A.Y1 : A.Y0;
+  const int le = nt - j;        // level eliminated by this pass (MODE 0, 1)
+  const int lb = nt - j + 1;    // level back-substituted (MODE 1, 2)
   const size_t tr = (size_t)nt * nxp;
-  const size_t at = (size_t)(l - 1) * nxp + m;    // time level l in trace layout
 
-  // node values and outgoing-data adjoints at this level
-  double u_hi = 0, u_hi_other = 0, lbo_top = 0, u_lo = 0, u_lo_other = 0, lbo_bot = 0;
-  if (st.has_top) {
-    u_hi = A.bands[((size_t)s * 2 + 0) * tr + at];
-    u_hi_other = A.bands[((size_t)s * 2 + 1) * tr + at];
-    lbo_top = A.lbar_out[((size_t)s * 2 + 1) * tr + at];
-  }
-  if (st.has_bot) {
-    u_lo = A.bands[((size_t)(s - 1) * 2 + 1) * tr + at];
-    u_lo_other = A.bands[((size_t)(s - 1) * 2 + 0) * tr + at];
-    lbo_bot = A.lbar_out[((size_t)(s - 1) * 2 + 0) * tr + at];
+  // interface-node data of both levels, one value per lane
+  double ue_top = 0, ue_top_o = 0, lbo_e_top = 0, ue_bot = 0, ue_bot_o = 0, lbo_e_bot = 0;
+  double ub_top = 0, lbo_b_top = 0, ub_bot = 0, lbo_b_bot = 0;
+  if (in_dom) {
+    if (st.has_top) {
+      const double* bl = A.bands + ((size_t)s * 2 + 0) * tr + m;
+      const double* bu = A.bands + ((size_t)s * 2 + 1) * tr + m;
+      const double* lo_ = A.lbar_out + ((size_t)s * 2 + 1) * tr + m;
+      if (MODE != 2) { ue_top = bl[(size_t)(le - 1) * nxp]; ue_top_o = bu[(size_t)(le - 1) * nxp]; lbo_e_top = lo_[(size_t)(le - 1) * nxp]; }
+      if (MODE != 0) { ub_top = bl[(size_t)(lb - 1) * nxp]; lbo_b_top = lo_[(size_t)(lb - 1) * nxp]; }
+    }
+    if (st.has_bot) {
+      const double* bu = A.bands + ((size_t)(s - 1) * 2 + 1) * tr + m;
+      const double* bl = A.bands + ((size_t)(s - 1) * 2 + 0) * tr + m;
+      const double* lo_ = A.lbar_out + ((size_t)(s - 1) * 2 + 0) * tr + m;
+      if (MODE != 2) { ue_bot = bu[(size_t)(le - 1) * nxp]; ue_bot_o = bl[(size_t)(le - 1) * nxp]; lbo_e_bot = lo_[(size_t)(le - 1) * nxp]; }
+      if (MODE != 0) { ub_bot = bu[(size_t)(lb - 1) * nxp]; lbo_b_bot = lo_[(size_t)(lb - 1) * nxp]; }
+    }
   }
 
-  // ascending elimination of A^T w = mu
-  double y_prev = 0.0;
-  for (int r = 0; r < L; ++r) {
-    const int i = lo + r;
-    const size_t e = (size_t)(st.rowoff + r) * nxp + m;
+  double w_prev = 0.0, y_prev = 0.0;
+  // rows go in groups of kPrefetch whose residues are loaded together, so that the
+  // loads of a group are in flight at once instead of one latency per row
+  constexpr int kPrefetch = 8;
+  for (int t0 = 0; t0 < L; t0 += kPrefetch) {
+  double ypre[kPrefetch], cpre[kPrefetch], gpre[kPrefetch], apre[kPrefetch], cabpre[kPrefetch];
+  int sgpre[kPrefetch];
+#pragma unroll
+  for (int u = 0; u < kPrefetch; ++u) {
+    const int t = t0 + u;
+    const int l = UP ? t : (L - 1 - t);
+    const bool ok = t < L;
+    ypre[u] = (MODE != 0 && ok) ? Ycur[(size_t)(st.rowoff + l) * P + col] : 0.0;
+    cpre[u] = ok ? cpB[l] : 0.0;
+    gpre[u] = ok ? gE[l] : 0.0;
+    apre[u] = ok ? aE[l] : 0.0;
+    cabpre[u] = ok ? A.cabs[lo + l] : 0.0;
+    sgpre[u] = ok ? A.sgn[lo + l] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPrefetch; ++u) {
+    const int t = t0 + u;
+    if (t >= L) break;  // uniform across the warp
+    const int l = UP ? t : (L - 1 - t);
+    const int i = lo + l;
+    double wv = 0.0;  // w^{le+1} (zero beyond nt)
+    if (MODE != 0) {
+      wv = ypre[u] - cpre[u] * w_prev;
+      w_prev = wv;
+      // ---- adjoint of the consumed data and the gradient terms at level lb ----
+      if (out_lane) {
+        if (st.has_top && l == L - 1) {
+          const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
+          const size_t at = (size_t)(lb - 1) * nxp + m;
+          A.lbar_in[((size_t)s * 2 + 0) * tr + at] = A.two_dt_hv * wr - lbo_b_top;
+          A.contrib[((size_t)s * 4 + 0) * tr + at] += -A.two_dt_hv * wr * ub_top + lbo_b_top * ub_top;
+          A.contrib[((size_t)s * 4 + 1) * tr + at] += lbo_b_top * ub_top;
+        }
+        if (st.has_bot && l == 0) {
+          const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
+          const size_t at = (size_t)(lb - 1) * nxp + m;
+          A.lbar_in[((size_t)(s - 1) * 2 + 1) * tr + at] = A.two_dt_hv * wr - lbo_b_bot;
+          A.contrib[((size_t)(s - 1) * 4 + 3) * tr + at] += -A.two_dt_hv * wr * ub_bot + lbo_b_bot * ub_bot;
+          A.contrib[((size_t)(s - 1) * 4 + 2) * tr + at] += lbo_b_bot * ub_bot;
+        }
+      }
+      if (MODE == 2) continue;
+    }
+    // ---- right-hand side of level le: E^T w^{le+1} + sources, then elimination ----
+    const int sg = sgpre[u];
+    const double wdn = shfl_val(wv, lane + sg);  // w^{le+1} of the downstream column
+    const double c = cabpre[u];
     double mu = 0.0;
-    if (have_next) {  // (E^T w^{l+1})_{i,m}
-      const double c = A.cabs[i];
-      const int sg = A.sgn[i];
-      if (adj_row_kind(A, st, i, m) != 1) mu += (1.0 - c) * wn[e];
-      if (sg > 0 && m + 1 <= A.nx && adj_row_kind(A, st, i, m + 1) != 1) mu += c * wn[e + 1];
-      if (sg < 0 && m - 1 >= 0 && adj_row_kind(A, st, i, m - 1) != 1) mu += c * wn[e - 1];
+    if (MODE != 0) {
+      if (!adj_identity(A, i, m, sg)) mu += (1.0 - c) * wv;
+      const int md = m + sg;
+      if (sg != 0 && md >= 0 && md <= A.nx && !adj_identity(A, i, md, sg)) mu += c * wdn;
     }
-    if (r == L - 1 && st.has_top) {
-      if (last_iterate) mu += 2.0 * A.dthx * (u_hi - u_hi_other);
-      mu += (st.p_top + st.q_top) * lbo_top;
+    if (st.has_top && l == L - 1) {
+      if (last_iterate) mu += 2.0 * A.dthx * (ue_top - ue_top_o);
+      mu += (st.p_top + st.q_top) * lbo_e_top;
     }
-    if (r == 0 && st.has_bot) {
-      if (last_iterate) mu += -2.0 * A.dthx * (u_lo_other - u_lo);
-      mu += (st.p_bot + st.q_bot) * lbo_bot;
+    if (st.has_bot && l == 0) {
+      if (last_iterate) mu += -2.0 * A.dthx * (ue_bot_o - ue_bot);
+      mu += (st.p_bot + st.q_bot) * lbo_e_bot;
     }
-    const double y = g[r] * (mu - sub[r] * y_prev);
-    A.scratch[e] = y;
+    const double y = gpre[u] * (mu - apre[u] * y_prev);
+    if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
     y_prev = y;
   }
-  // descending back-substitution
-  double w_next = 0.0, w_top = 0.0, w_bot = 0.0;
-  for (int r = L - 1; r >= 0; --r) {
-    const size_t e = (size_t)(st.rowoff + r) * nxp + m;
-    const double w = A.scratch[e] - cp[r] * w_next;
-    wc[e] = w;
-    w_next = w;
-    if (r == L - 1) w_top = w;
-    if (r == 0) w_bot = w;
-  }
-  // adjoint of the consumed data and gradient contributions
-  if (st.has_top) {
-    const double wr = adj_row_kind(A, st, st.hi, m) == 2 ? w_top : 0.0;
-    A.lbar_in[((size_t)s * 2 + 0) * tr + at] = A.two_dt_hv * wr - lbo_top;
-    A.contrib[((size_t)s * 4 + 0) * tr + at] += -A.two_dt_hv * wr * u_hi + lbo_top * u_hi;
-    A.contrib[((size_t)s * 4 + 1) * tr + at] += lbo_top * u_hi;
-  }
-  if (st.has_bot) {
-    const double wr = adj_row_kind(A, st, st.lo, m) == 3 ? w_bot : 0.0;
-    A.lbar_in[((size_t)(s - 1) * 2 + 1) * tr + at] = A.two_dt_hv * wr - lbo_bot;
-    A.contrib[((size_t)(s - 1) * 4 + 3) * tr + at] += -A.two_dt_hv * wr * u_lo + lbo_bot * u_lo;
-    A.contrib[((size_t)(s - 1) * 4 + 2) * tr + at] += lbo_bot * u_lo;
   }
 }
 

@@ -75,25 +75,52 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   }
 
   T w_prev = T(0), y_prev = T(0), zm1 = T(0), zm2 = T(0);
+  T g_last = T(0), a_last = T(0);  // factors of the previous row in pass order
   // elimination of local row l from the M-weighted right-hand side rhs
-  auto eliminate = [&](int l, T rhs) {
+  auto eliminate = [&](int l, T rhs, T gl, T al) {
     const bool top_end = l == L - 1, bot_end = l == 0;
     T R = rhs;
     if (top_end && st.has_top) R = A.robin ? (T)((double)R + E.dt * lam_rhs_top) : (T)lam_rhs_top;
     if (bot_end && st.has_bot) R = A.robin ? (T)((double)R + E.dt * lam_rhs_bot) : (T)lam_rhs_bot;
-    const T y = gE[l] * (R - aE[l] * y_prev);
+    const T y = gl * (R - al * y_prev);
     if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
     y_prev = y;
   };
 
-  for (int t = 0; t < L; ++t) {
+  // rows go in groups of kPrefetch whose inputs are loaded together, so that the
+  // loads of a group are in flight at once instead of one latency per row
+  constexpr int kPrefetch = 8;
+  for (int t0 = 0; t0 < L; t0 += kPrefetch) {
+  T ypre[kPrefetch], fpre[kPrefetch], cppre[kPrefetch], gpre[kPrefetch], apre[kPrefetch], cabpre[kPrefetch];
+  int sgpre[kPrefetch];
+#pragma unroll
+  for (int u = 0; u < kPrefetch; ++u) {
+    const int t = t0 + u;
     const int l = UP ? t : (L - 1 - t);
     const int i = lo + l;
-    T u;
+    const bool ok = t < L;
+    ypre[u] = !ok ? T(0) : (MODE == 0 ? A.U0[(size_t)i * P + col] : Ycur[(size_t)(st.rowoff + l) * P + col]);
+    T f = T(0);
+    if (MODE != 2 && ok)
+      for (int r = 0; r < A.nforce; ++r)
+        f += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
+    fpre[u] = f;
+    cppre[u] = ok ? cpB[l] : T(0);
+    gpre[u] = ok ? gE[l] : T(0);
+    apre[u] = ok ? aE[l] : T(0);
+    cabpre[u] = ok ? A.cabs[i] : T(0);
+    sgpre[u] = ok ? A.sgn[i] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPrefetch; ++u) {
+    const int t = t0 + u;
+    if (t >= L) break;  // uniform across the warp
+    const int l = UP ? t : (L - 1 - t);
+    T u_;
     if (MODE == 0) {
-      u = A.U0[(size_t)i * P + col];
+      u_ = ypre[u];
     } else {
-      const T wv = Ycur[(size_t)(st.rowoff + l) * P + col] - cpB[l] * w_prev;
+      const T wv = ypre[u] - cppre[u] * w_prev;
       const T wlast = w_prev;  // w of the previous row in pass order
       w_prev = wv;
       // ---- outgoing interface data of t^k from w^k ----
@@ -135,24 +162,22 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
         }
       }
       // ---- transport over dt: u^k = w^k - c (w^k - w^k upstream) ----
-      const T wnb = shfl_val(wv, lane - A.sgn[i]);
-      u = wv - A.cabs[i] * (wv - wnb);
+      const T wnb = shfl_val(wv, lane - sgpre[u]);
+      u_ = wv - cabpre[u] * (wv - wnb);
       // ---- overlap values of u^k ----
       if (out_lane) {
         if (st.has_top && l >= aT && l <= aT + ov)
-          A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)u;
+          A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)u_;
         if (st.has_bot && l >= aB && l <= aB + ov)
-          A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)u;
+          A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)u_;
       }
       if (MODE == 2) {
-        if (out_lane) A.UT[(size_t)(st.rowoff + l) * P + col] = u;
+        if (out_lane) A.UT[(size_t)(st.rowoff + l) * P + col] = u_;
         continue;
       }
     }
     // ---- z^{k+1} = u^k + dt f^{k+1}; keep it at the trace rows for the next pass ----
-    T z = u;
-    for (int r = 0; r < A.nforce; ++r)
-      z += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
+    const T z = u_ + fpre[u];
     if (robin_ov && out_lane) {  // halo lanes hold a wrong u (their upstream lane is missing)
       if (st.has_top && (l == aT || l == aT - 1)) znext[(size_t)(0 * 2 + (aT - l)) * nxp + m] = (double)z;
       if (st.has_bot && (l == bB || l == bB + 1)) znext[(size_t)(1 * 2 + (l - bB)) * nxp + m] = (double)z;
@@ -162,15 +187,18 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
       const int lp = UP ? t - 1 : L - t;
       const T rhs = (t == 1) ? (T)(E.m_half * (double)zm1 + E.m_off * (double)z)  // end row: one element
                              : (T)(E.m_off * (double)zm2 + E.m_full * (double)zm1 + E.m_off * (double)z);
-      eliminate(lp, rhs);
+      eliminate(lp, rhs, g_last, a_last);
     }
     zm2 = zm1;
     zm1 = z;
+    g_last = gpre[u];
+    a_last = apre[u];
+  }
   }
   if (MODE != 2) {
     // the last row in pass order: an end row (one element)
     const T rhs = (L == 1) ? (T)(E.m_half * (double)zm1) : (T)(E.m_half * (double)zm1 + E.m_off * (double)zm2);
-    eliminate(UP ? L - 1 : 0, rhs);
+    eliminate(UP ? L - 1 : 0, rhs, g_last, a_last);
   }
 }
 

@@ -166,7 +166,9 @@ void split_rows(const Geometry& g, const kfp::StripInfo& st, double* a, double* 
 // three column classes (m = 0, interior, m = nx) and both elimination directions.
 // Layout [S][3][2][3][Lmax]: field 0 = 1/pivot, 1 = coupling to the previously
 // eliminated row, 2 = back-substitution coefficient.
-std::vector<double> build_factors(const Geometry& g) {
+// transposed: the factors of A^T (sub-diagonal c_{l-1}, super-diagonal a_{l+1}) for
+// the fused adjoint pass.
+std::vector<double> build_factors(const Geometry& g, bool transposed = false) {
   std::vector<double> coef((size_t)g.S * 3 * 2 * 3 * g.Lmax, 0.0);
   std::vector<double> a(g.Lmax), b(g.Lmax), c(g.Lmax), cp(g.Lmax);
   const double r = g.r;
@@ -192,6 +194,14 @@ std::vector<double> build_factors(const Geometry& g) {
           continue;
         }
         a[l] = -r; b[l] = 1 + 2 * r; c[l] = -r;
+      }
+      if (transposed) {
+        std::vector<double> at(L), ct(L);
+        for (int l = 0; l < L; ++l) {
+          at[l] = l > 0 ? c[l - 1] : 0.0;
+          ct[l] = l < L - 1 ? a[l + 1] : 0.0;
+        }
+        for (int l = 0; l < L; ++l) { a[l] = at[l]; c[l] = ct[l]; }
       }
       double* up = &coef[(((size_t)s * 3 + kappa) * 2 + 0) * 3 * g.Lmax];
       double* dn = &coef[(((size_t)s * 3 + kappa) * 2 + 1) * 3 * g.Lmax];
@@ -287,9 +297,8 @@ struct kfp_swr {
   double* adj_bands = nullptr;   // [K][S-1][2][nt][nx+1]
   double* adj_lbar = nullptr;    // [2][S-1][2][nt][nx+1]
   double* adj_contrib = nullptr; // [S-1][4][nt][nx+1]
-  double* adj_w = nullptr;       // [2][rows][nx+1]
-  double* adj_scratch = nullptr; // [rows][nx+1]
-  double* adj_fac = nullptr;     // [S][3][3][Lmax]
+  double* adj_w = nullptr;       // [2][rows][P] elimination residue of the adjoint passes
+  double* adj_fac = nullptr;     // [S][3][2][3][Lmax] LU factors of A^T
   double* adj_grad = nullptr;    // [S-1][2]
   int adj_K = 0;
   cudaStream_t cap_stream = nullptr;
@@ -729,7 +738,7 @@ struct kfp_swr {
       if (e) cudaEventDestroy(e);
     void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, zrec, partial, tickets, scal, hist, iter, stage, d_res,
-                    adj_bands, adj_lbar, adj_contrib, adj_w, adj_scratch, adj_fac, adj_grad};
+                    adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (host_scal) cudaFreeHost(host_scal);
@@ -1144,42 +1153,6 @@ kfp_status create_inner(kfp_swr* h, const kfp_swr_desc* d) {
   return KFP_OK;
 }
 
-// Transposed implicit-Euler factors for the adjoint: per strip and column class,
-// ascending elimination of A^T (sub-diagonal c_{r-1}, super-diagonal a_{r+1}).
-std::vector<double> build_adjoint_factors(const Geometry& g) {
-  std::vector<double> fac((size_t)g.S * 3 * 3 * g.Lmax, 0.0);
-  std::vector<double> a(g.Lmax), b(g.Lmax), c(g.Lmax), cpv(g.Lmax);
-  const double r = g.r;
-  for (int s = 0; s < g.S; ++s) {
-    const kfp::StripInfo& st = g.strips[s];
-    const int L = st.L;
-    for (int cls = 0; cls < 3; ++cls) {
-      for (int l = 0; l < L; ++l) {
-        const int i = st.lo + l;
-        const double vi = g.v0 + i * g.hv;
-        const bool inflow = (cls == 0 && vi > 0) || (cls == 2 && vi < 0);
-        const bool top = st.has_top && i == st.hi, bot = st.has_bot && i == st.lo;
-        a[l] = 0.0; b[l] = 1.0; c[l] = 0.0;
-        if (i == 0 || i == g.nv || inflow) continue;
-        if (top) { a[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.p_top * g.dt / g.hv; continue; }
-        if (bot) { c[l] = -2 * r; b[l] = 1 + 2 * r + 2 * st.q_bot * g.dt / g.hv; continue; }
-        a[l] = -r; b[l] = 1 + 2 * r; c[l] = -r;
-      }
-      double* f = &fac[((size_t)s * 3 + cls) * 3 * g.Lmax];
-      for (int l = 0; l < L; ++l) {
-        const double sub = l > 0 ? c[l - 1] : 0.0, sup = l < L - 1 ? a[l + 1] : 0.0;
-        const double piv = b[l] - (l > 0 ? sub * cpv[l - 1] : 0.0);
-        const double gi = 1.0 / piv;
-        cpv[l] = sup * gi;
-        f[0 * g.Lmax + l] = gi;
-        f[1 * g.Lmax + l] = sub;
-        f[2 * g.Lmax + l] = cpv[l];
-      }
-    }
-  }
-  return fac;
-}
-
 kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
                          double* grad_q) {
   Geometry& g = h->g;
@@ -1189,14 +1162,14 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
                    "the adjoint needs FP64, Robin transmission, no overlap, >= 2 strips and the parallel form");
   if (K < 1) return h->fail(KFP_EINVAL, "need K >= 1");
   const size_t nxp = g.nx + 1, per = (size_t)g.nt * nxp, ntr = h->n_trace;
-  const size_t field = (size_t)g.rows * nxp;
   kfp_status rc;
+  const size_t ystate = (size_t)g.rows * g.P;
+  const size_t nfac = (size_t)g.S * 3 * 2 * 3 * g.Lmax;
   if (!h->adj_lbar) {
     if ((rc = alloc(h, (void**)&h->adj_lbar, sizeof(double) * 2 * ntr))) return rc;
     if ((rc = alloc(h, (void**)&h->adj_contrib, sizeof(double) * (size_t)(g.S - 1) * 4 * per))) return rc;
-    if ((rc = alloc(h, (void**)&h->adj_w, sizeof(double) * 2 * field))) return rc;
-    if ((rc = alloc(h, (void**)&h->adj_scratch, sizeof(double) * field))) return rc;
-    if ((rc = alloc(h, (void**)&h->adj_fac, sizeof(double) * (size_t)g.S * 9 * g.Lmax))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_w, sizeof(double) * 2 * ystate))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_fac, sizeof(double) * nfac))) return rc;
     if ((rc = alloc(h, (void**)&h->adj_grad, sizeof(double) * 2 * (g.S - 1)))) return rc;
   }
   if (K > h->adj_K) {
@@ -1205,7 +1178,7 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
     if ((rc = alloc(h, (void**)&h->adj_bands, sizeof(double) * (size_t)K * ntr))) return rc;
     h->adj_K = K;
   }
-  std::vector<double> fac = build_adjoint_factors(g);
+  std::vector<double> fac = build_factors(g, true);
   KFP_CUDA_TRY_H(cudaMemcpy(h->adj_fac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice));
   // forward: K iterations from lambda^0, keeping every iterate's interface-node values
   if (lam0) {
@@ -1228,28 +1201,36 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   // adjoint, backward over iterates and time levels
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_lbar, 0, sizeof(double) * 2 * ntr, h->stream));
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_contrib, 0, sizeof(double) * (size_t)(g.S - 1) * 4 * per, h->stream));
-  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_w, 0, sizeof(double) * 2 * field, h->stream));
-  kfp::AdjArgs A;
-  A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.S = g.S; A.Lmax = g.Lmax;
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_w, 0, sizeof(double) * 2 * ystate, h->stream));
+  kfp::AdjPassArgs A;
+  A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.P = g.P; A.W = g.W; A.Lmax = g.Lmax;
   A.two_dt_hv = 2.0 * g.dt / g.hv;
   A.dthx = g.dt * g.hx;
   A.strips = h->strips;
-  A.fac = h->adj_fac;
+  A.coef = h->adj_fac;
   A.cabs = (const double*)h->cabs;
   A.sgn = h->sgn;
   A.contrib = h->adj_contrib;
-  A.w0 = h->adj_w;
-  A.w1 = h->adj_w + field;
-  A.scratch = h->adj_scratch;
-  A.rows = g.rows;
+  A.Y0 = h->adj_w;
+  A.Y1 = h->adj_w + ystate;
   double* lb_out = h->adj_lbar;
   double* lb_in = h->adj_lbar + ntr;
-  const dim3 grid((unsigned)((nxp + 127) / 128), g.S);
+  const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
+  const dim3 block(kfp::kWarpsPerBlock * 32);
+  // per iterate, from the last: pass j back-substitutes level nt-j+1 and eliminates
+  // level nt-j, in ascending row order when j is even
   for (int k = K; k >= 1; --k) {
     A.bands = h->adj_bands + (size_t)(k - 1) * ntr;
     A.lbar_out = lb_out;
     A.lbar_in = lb_in;
-    for (int l = g.nt; l >= 1; --l) kfp::adjoint_level_kernel<<<grid, 128, 0, h->stream>>>(A, l, k == K ? 1 : 0);
+    const int last = k == K ? 1 : 0;
+    kfp::adjoint_pass_kernel<true, 0><<<grid, block, 0, h->stream>>>(A, 0, last);
+    for (int j = 1; j < g.nt; ++j) {
+      if (j & 1) kfp::adjoint_pass_kernel<false, 1><<<grid, block, 0, h->stream>>>(A, j, last);
+      else       kfp::adjoint_pass_kernel<true, 1><<<grid, block, 0, h->stream>>>(A, j, last);
+    }
+    if (g.nt & 1) kfp::adjoint_pass_kernel<false, 2><<<grid, block, 0, h->stream>>>(A, g.nt, last);
+    else          kfp::adjoint_pass_kernel<true, 2><<<grid, block, 0, h->stream>>>(A, g.nt, last);
     std::swap(lb_out, lb_in);
   }
   kfp::gradient_reduce_kernel<<<2 * (g.S - 1), kfp::kReduceThreads, 0, h->stream>>>(h->adj_contrib, per,

@@ -8,6 +8,9 @@
   of the one-sided Robin parameter p (Section 6.4.1, Figure 1).
 * ``pq_scan``: the same over a grid of two-sided parameters (p, q) (Section 6.4.2,
   Figure 2).
+* ``mixed_precision``: the mixed-precision workload (4096 x 8192 cells, 16 Robin
+  strips, 4000 steps) run to e_mis < 1e-8 in the mixed form and in plain FP64, with
+  the wall times, the iteration counts and the difference of the two results.
 
 Every run solves the error equation of the model problem (Section 6.1: periodic in
 x, zero flux in v, f = 0, u0 = 0, T = 2) on two strips split at v = 0 from a random
@@ -24,6 +27,7 @@ Command line::
     python -m paper_1306_4596_gb300.experiments table1 --levels 0 1 2
     python -m paper_1306_4596_gb300.experiments pscan --j 0 --p 2 8 0.25
     python -m paper_1306_4596_gb300.experiments pqscan --j 0 --p 2 14 1 --q 1 6 0.5
+    python -m paper_1306_4596_gb300.experiments mixed
 """
 from __future__ import annotations
 
@@ -144,6 +148,46 @@ def pq_scan(ps: Iterable[float], qs: Iterable[float], **kw) -> List[Dict]:
     return rows
 
 
+def mixed_precision(tol: float = 1e-8, max_f64: int = 400, max_mixed: int = 40, log=None) -> Dict:
+    """Time to e_mis < tol on the mixed-precision workload, mixed form against plain
+    FP64 (both from lambda^0 = 0, CUDA graphs, inputs on the device), plus the FP32
+    per-iteration time, and the maximum differences of the two results (solution at
+    T and interface data) relative to the FP64 ones."""
+    import torch
+    prob = inputs.mixed_precision_workload()
+    out = {"workload": "Nx=4096, Nv=8192, 16 Robin strips p=4, dt=5e-5, Nt=4000, Gaussian bumps (seed 4)",
+           "cell_updates_per_iteration": _swr.cell_updates_per_iteration(prob), "tol": tol}
+    res = {}
+    for prec, cap in (("mixed", max_mixed), ("f64", max_f64)):
+        with _swr.SWR(prob, prec, inputs_on="device") as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.sweep(cap, tol, 1)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            e = s.error()
+            cnt = s.counters()
+            res[prec] = (s.solution(), s.traces())
+        out[prec] = {"seconds": el, "fp64_iterations": cnt["fp64_iterations"],
+                     "fp32_iterations": cnt["fp32_iterations"], "e_mis": float(e[0]), "reached": bool(e[0] < tol)}
+        if log:
+            log(json.dumps({prec: out[prec]}))
+    with _swr.SWR(prob, "f32", inputs_on="device") as s:
+        s.sweep(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.sweep(3)
+        torch.cuda.synchronize()
+        out["f32_seconds_per_iteration"] = (time.perf_counter() - t0) / 3
+    out["f64_seconds_per_iteration"] = out["f64"]["seconds"] / max(out["f64"]["fp64_iterations"], 1)
+    (um, lm), (u64, l64) = res["mixed"], res["f64"]
+    out["max_rel_diff_solution"] = float(np.abs(um - u64).max() / np.abs(u64).max())
+    out["max_rel_diff_traces"] = float(np.abs(lm - l64).max() / np.abs(l64).max())
+    if out["mixed"]["reached"] and out["f64"]["reached"]:
+        out["speedup_mixed_vs_f64"] = out["f64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
 def _range(spec: List[float]) -> np.ndarray:
     lo, hi, step = spec
     return np.round(np.arange(lo, hi + 0.5 * step, step), 10)
@@ -156,6 +200,9 @@ def main(argv=None) -> int:
     t.add_argument("--levels", type=int, nargs="+", default=[0, 1, 2, 3, 4])
     t.add_argument("--methods", nargs="+", default=None, choices=list(METHODS))
     t.add_argument("--max-iters", type=int, default=MAX_ITERS)
+    mx = sub.add_parser("mixed")
+    mx.add_argument("--tol", type=float, default=1e-8)
+    mx.add_argument("--max-f64", type=int, default=400)
     for name in ("pscan", "pqscan"):
         sp = sub.add_parser(name)
         sp.add_argument("--j", type=int, default=0)
@@ -163,14 +210,16 @@ def main(argv=None) -> int:
         sp.add_argument("--p", type=float, nargs=3, default=[2.0, 8.0, 0.25], metavar=("LO", "HI", "STEP"))
         if name == "pqscan":
             sp.add_argument("--q", type=float, nargs=3, default=[1.0, 6.0, 0.5], metavar=("LO", "HI", "STEP"))
-    for sp in sub.choices.values():
+    for sp in (t, sub.choices["pscan"], sub.choices["pqscan"]):
         sp.add_argument("--parallel", action="store_true", help="parallel form instead of the serial order")
         sp.add_argument("--seed", type=int, default=7)
         sp.add_argument("--precision", default="f64", choices=["f64", "f32"])
         sp.add_argument("--scheme", type=int, default=0, choices=[0, 1],
                         help="0: implicit Euler + upwind; 1: the Lie splitting with P1 elements")
     a = ap.parse_args(argv)
-    if a.cmd == "table1":
+    if a.cmd == "mixed":
+        print(json.dumps(mixed_precision(a.tol, a.max_f64, log=lambda s: print(s, flush=True))), flush=True)
+    elif a.cmd == "table1":
         rows = table1(a.levels, a.parallel, a.seed, a.max_iters, a.precision, a.methods,
                       log=lambda s: print(s, flush=True), scheme=a.scheme)
         print(format_table1(rows, a.max_iters))
