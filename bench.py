@@ -193,6 +193,20 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def max_over_ranks(torch, dist, world: int, ms: float, device: str = "cuda") -> float:
+    """The slowest rank's time: the job's time when every rank runs its own replica."""
+    if world <= 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, cells_per_iter: int, steps: int, ms: float) -> float:
+    """Whole-job cell-updates/s: every rank advances its own replica by `steps` iterations."""
+    return world * cells_per_iter * steps / (ms / 1e3)
+
+
 def time_iterations(torch, solver, steps: int, warmup: int, dist, world: int, device_index: int):
     for _ in range(warmup):
         solver.sweep(1)
@@ -208,11 +222,7 @@ def time_iterations(torch, solver, steps: int, warmup: int, dist, world: int, de
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, world, start.elapsed_time(end))
     return ms, clocks.summary()
 
 
@@ -273,7 +283,7 @@ def main():
     e_hist = solver.error()[3]
     solver.close()
 
-    value = world * cells_per_iter * args.steps / (ms / 1e3)
+    value = job_rate(world, cells_per_iter, args.steps, ms)
     ms_per_step = ms / args.steps
     cells_per_pass = cells_per_iter / prob.nt  # every pass advances every strip node once
     peaks = measured_peaks()
