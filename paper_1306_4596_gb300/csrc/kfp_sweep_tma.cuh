@@ -339,16 +339,19 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
     const int l1 = l0 + kChunk - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
                                            (rloT <= rhiT && !(l1 < rloT || l0 > rhiT)));
-    // Chunks that reach outside the strip, caller boundary data, and the chunks holding
-    // the v = 0 row or a change of the upwind side go through the general path.  Every
-    // other chunk is a run of 16 rows with no per-row branch: its recorded rows are
-    // written after the back-substitution chain, and the strip's end rows (interface
-    // data) are folded into the chain's first or last term.
+    // Chunks that reach outside the strip, caller boundary data, and chunks in which
+    // the upwind side changes (v changes sign inside) go through the general path.
+    // Every other chunk is a run of 16 rows with no per-row branch: its recorded rows
+    // are written after the back-substitution chain, and the strip's end rows
+    // (interface data) are folded into the chain's first or last term.  A v = 0 row at
+    // either end of a chunk has no transport (its upwind coefficient is 0), so it takes
+    // the chunk's neighbour lane like the other rows.
     const int sg_first = slot_int(sm.rec[q][0][cls * 8 + 6]);
     const int sg_last = slot_int(sm.rec[q][kChunk - 1][cls * 8 + 6]);
-    const bool general = X.bc_data || l0 < 0 || l1 >= L || sg_first != sg_last || sg_first == 0;
+    const bool general = X.bc_data || l0 < 0 || l1 >= L || sg_first * sg_last < 0;
     if (!general) {
-      const int src = lane - sg_first;  // upwind neighbour lane for the whole chunk
+      // upwind neighbour lane for the whole chunk
+      const int src = lane - (sg_first != 0 ? sg_first : sg_last);
       const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
       const int cbase = wl * kOutCols + lane;
       // (A) back-substitution chain of this chunk, interleaved with the deferred
