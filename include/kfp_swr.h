@@ -231,6 +231,18 @@ kfp_status kfp_swr_set_robin(kfp_swr_t h, const double* p, const double* q);
 kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx, double dt,
                                    double hx, double* out, void* cuda_stream);
 
+/*
+ * Check of the bounded device waits; the paper has no counterpart.  Every wait of
+ * the sweep kernels on an mbarrier phase gives up after a limit, raises a flag and
+ * returns, and the host then reports KFP_ETIMEOUT with the context still usable.
+ * This runs that path on purpose without faulting anything: one block polls, at most
+ * `limit` times, an mbarrier phase that nothing completes.  Enqueued on cuda_stream
+ * and synchronised.  Returns KFP_ETIMEOUT when the wait gave up as designed (KFP_OK
+ * would mean the phase completed, which cannot happen); KFP_EINVAL for limit == 0;
+ * KFP_ENOMEM, KFP_ECUDA.
+ */
+kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream);
+
 /* Iteration counters (any pointer may be NULL): iterations whose strip solves ran
  * in FP64 and in FP32 (for KFP_MIXED: outer FP64 steps and inner FP32 correction
  * iterations), and -- with KFP_FLAG_PROFILE -- the summed device time of the FP32

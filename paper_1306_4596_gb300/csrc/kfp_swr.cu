@@ -1810,3 +1810,47 @@ const char* kfp_batch_last_error(kfp_batch_t b) { return b ? b->last_error.c_str
 const char* kfp_swr_create_error(void) { return g_create_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Check of the bounded device waits (no counterpart in the paper): one block polls
+// an mbarrier phase that nothing completes, with the primitives of the sweep ring.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__global__ void bounded_wait_selftest_kernel(int* flag, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    kfp::mbar_init(&bar, 1);  // one arrival expected; none comes
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool done = false;
+    for (unsigned it = 0; it < limit && !done; ++it) done = kfp::mbar_try_wait(&bar, 0);
+    *flag = done ? 0 : 1;
+  }
+}
+
+}  // namespace
+
+extern "C" kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream) {
+  if (limit == 0) return KFP_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return KFP_ENOMEM;
+  }
+  int h = -1;
+  cudaError_t e = cudaMemsetAsync(flag, 0xff, sizeof(int), st);
+  if (e == cudaSuccess) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(flag, limit);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  if (e != cudaSuccess) return KFP_ECUDA;
+  return h == 1 ? KFP_ETIMEOUT : (h == 0 ? KFP_OK : KFP_ECUDA);
+}

@@ -38,7 +38,8 @@ EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_tr
             "kfp_swr_bands", "kfp_swr_solution", "kfp_swr_stats", "kfp_swr_destroy",
             "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters",
             "kfp_batch_create", "kfp_batch_configure", "kfp_batch_sweep", "kfp_batch_instance", "kfp_batch_stats",
-            "kfp_batch_destroy", "kfp_batch_last_error", "kfp_swr_gradient", "kfp_swr_set_robin")
+            "kfp_batch_destroy", "kfp_batch_last_error", "kfp_swr_gradient", "kfp_swr_set_robin",
+            "kfp_selftest_bounded_wait")
 KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -223,6 +224,14 @@ def kfp_iface_norms_noalloc(bands_ptr: int, nif: int, nt: int, overlap_cells: in
         else:
             msg = "device set-up or kernel launch failed"
         raise KfpError(st, f"kfp_iface_norms_noalloc: {msg}")
+
+
+def kfp_selftest_bounded_wait(limit: int = 1 << 16, cuda_stream: int = 0) -> int:
+    """Run the bounded-wait check (see the header); returns the status, KFP_ETIMEOUT
+    when the wait gave up as designed."""
+    lib = load()
+    lib.kfp_selftest_bounded_wait.argtypes = [ctypes.c_uint, ctypes.c_void_p]
+    return int(lib.kfp_selftest_bounded_wait(limit, cuda_stream))
 
 
 def kfp_swr_last_error(h: int) -> str:
