@@ -70,6 +70,14 @@ def test_validation_without_gpu():
     assert st == swr.KFP_EINVAL and "> 0" in msg
     st, h, msg = _create_status(_desc(prob, nx=0), prob)
     assert st == swr.KFP_EINVAL
+    # the split scheme of Section 6.2 is built for the model problem only
+    st, h, msg = _create_status(_desc(prob, flags=swr.KFP_FLAG_SPLIT_SCHEME), prob)
+    assert st == swr.KFP_EINVAL and h is None and "split" in msg
+    st, h, msg = _create_status(_desc(prob, flags=swr.KFP_FLAG_SPLIT_SCHEME | swr.KFP_FLAG_NEUMANN_V), prob)
+    assert st == swr.KFP_EINVAL and "split" in msg
+    tiny = inputs.random_data(1, 8, 2, 0.1, 2, 1, False, seed=0)
+    st, h, msg = _create_status(_desc(tiny, flags=swr.KFP_FLAG_PERIODIC_X), tiny)
+    assert st == swr.KFP_EINVAL and "periodic" in msg
 
 
 def test_null_arguments_are_rejected():
