@@ -46,7 +46,7 @@ UNIT = "cell-updates/s"
 WORKLOAD = ("SWR at scale: x in [0,1], v in [-4,4], Nx=2048, Nv=4096, 8 v-strips, Robin p=4 "
             "(no overlap), dt=1e-4, Nt=2000, 16 seeded Gaussian bumps (seed 2)")
 
-# Algorithmic work of one cell-update ("Roofline"):
+# Algorithmic work of one cell-update of the fused sweep pass (one node advanced one step):
 FP64_FLOPS_PER_CELL = 8    # 4 fused multiply-adds: transport (2), elimination (1), back-substitution (1)
 BYTES_PER_CELL = {"f64": 24, "f32": 12}  # read y^k, read F, write y^{k+1}
 # FP64 pipe of sm_103a: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flops x 2.07 GHz
