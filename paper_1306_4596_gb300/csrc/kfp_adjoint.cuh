@@ -105,22 +105,33 @@ adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
   double w_prev = 0.0, y_prev = 0.0;
   // rows go in groups of kPrefetch whose residues are loaded together, so that the
   // loads of a group are in flight at once instead of one latency per row
-  constexpr int kPrefetch = 8;
+  // (the inputs of the next group are loaded while the current one is computed)
+  constexpr int kPrefetch = 4;
+  double ynx[kPrefetch], cnx[kPrefetch], gnx[kPrefetch], anx[kPrefetch], cabnx[kPrefetch];
+  int sgnx[kPrefetch];
+  auto load_group = [&](int tb) {
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int t = tb + u;
+      const bool ok = t < L;
+      const int l = ok ? (UP ? t : (L - 1 - t)) : 0;
+      ynx[u] = (MODE != 0 && ok) ? Ycur[(size_t)(st.rowoff + l) * P + col] : 0.0;
+      cnx[u] = ok ? cpB[l] : 0.0;
+      gnx[u] = ok ? gE[l] : 0.0;
+      anx[u] = ok ? aE[l] : 0.0;
+      cabnx[u] = ok ? A.cabs[lo + l] : 0.0;
+      sgnx[u] = ok ? A.sgn[lo + l] : 0;
+    }
+  };
+  load_group(0);
   for (int t0 = 0; t0 < L; t0 += kPrefetch) {
   double ypre[kPrefetch], cpre[kPrefetch], gpre[kPrefetch], apre[kPrefetch], cabpre[kPrefetch];
   int sgpre[kPrefetch];
 #pragma unroll
   for (int u = 0; u < kPrefetch; ++u) {
-    const int t = t0 + u;
-    const int l = UP ? t : (L - 1 - t);
-    const bool ok = t < L;
-    ypre[u] = (MODE != 0 && ok) ? Ycur[(size_t)(st.rowoff + l) * P + col] : 0.0;
-    cpre[u] = ok ? cpB[l] : 0.0;
-    gpre[u] = ok ? gE[l] : 0.0;
-    apre[u] = ok ? aE[l] : 0.0;
-    cabpre[u] = ok ? A.cabs[lo + l] : 0.0;
-    sgpre[u] = ok ? A.sgn[lo + l] : 0;
+    ypre[u] = ynx[u]; cpre[u] = cnx[u]; gpre[u] = gnx[u]; apre[u] = anx[u]; cabpre[u] = cabnx[u]; sgpre[u] = sgnx[u];
   }
+  if (t0 + kPrefetch < L) load_group(t0 + kPrefetch);
 #pragma unroll
   for (int u = 0; u < kPrefetch; ++u) {
     const int t = t0 + u;

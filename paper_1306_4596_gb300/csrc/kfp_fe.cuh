@@ -76,6 +76,7 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
 
   T w_prev = T(0), y_prev = T(0), zm1 = T(0), zm2 = T(0);
   T g_last = T(0), a_last = T(0);  // factors of the previous row in pass order
+  T w_last = T(0);                 // w of the previous row in pass order
   // elimination of local row l from the M-weighted right-hand side rhs
   auto eliminate = [&](int l, T rhs, T gl, T al) {
     const bool top_end = l == L - 1, bot_end = l == 0;
@@ -87,54 +88,85 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
     y_prev = y;
   };
 
-  // rows go in groups of kPrefetch whose inputs are loaded together, so that the
-  // loads of a group are in flight at once instead of one latency per row
-  constexpr int kPrefetch = 8;
-  for (int t0 = 0; t0 < L; t0 += kPrefetch) {
-  T ypre[kPrefetch], fpre[kPrefetch], cppre[kPrefetch], gpre[kPrefetch], apre[kPrefetch], cabpre[kPrefetch];
-  int sgpre[kPrefetch];
+  // Rows go in groups of kGroup.  The inputs of the next group are loaded while the
+  // current one is computed (two register buffers), then per group: (A) the
+  // back-substitution chain, (B) the transport, z and the overlap values of every row
+  // of the group (independent of each other), (C) the elimination chain of the rows
+  // whose right-hand side is complete.
+  constexpr int kGroup = 4;
+  T ynx[kGroup], f0nx[kGroup], cpnx[kGroup], gnx[kGroup], anx[kGroup], cabnx[kGroup];
+  int sgnx[kGroup];
+  const T dta0 = (MODE != 2 && A.nforce > 0) ? (T)A.dta[(size_t)k1 * A.nforce] : T(0);
+  auto load_group = [&](int tb) {
 #pragma unroll
-  for (int u = 0; u < kPrefetch; ++u) {
-    const int t = t0 + u;
-    const int l = UP ? t : (L - 1 - t);
-    const int i = lo + l;
-    const bool ok = t < L;
-    ypre[u] = !ok ? T(0) : (MODE == 0 ? A.U0[(size_t)i * P + col] : Ycur[(size_t)(st.rowoff + l) * P + col]);
-    T f = T(0);
-    if (MODE != 2 && ok)
-      for (int r = 0; r < A.nforce; ++r)
-        f += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
-    fpre[u] = f;
-    cppre[u] = ok ? cpB[l] : T(0);
-    gpre[u] = ok ? gE[l] : T(0);
-    apre[u] = ok ? aE[l] : T(0);
-    cabpre[u] = ok ? A.cabs[i] : T(0);
-    sgpre[u] = ok ? A.sgn[i] : 0;
-  }
+    for (int u = 0; u < kGroup; ++u) {
+      const int t = tb + u;
+      const bool ok = t < L;
+      const int l = ok ? (UP ? t : (L - 1 - t)) : 0;
+      const int i = lo + l;
+      ynx[u] = !ok ? T(0) : (MODE == 0 ? A.U0[(size_t)i * P + col] : Ycur[(size_t)(st.rowoff + l) * P + col]);
+      f0nx[u] = (MODE != 2 && ok && A.nforce > 0) ? A.F[(size_t)i * P + col] : T(0);
+      cpnx[u] = ok ? cpB[l] : T(0);
+      gnx[u] = ok ? gE[l] : T(0);
+      anx[u] = ok ? aE[l] : T(0);
+      cabnx[u] = ok ? A.cabs[i] : T(0);
+      sgnx[u] = ok ? A.sgn[i] : 0;
+    }
+  };
+  load_group(0);
+  for (int t0 = 0; t0 < L; t0 += kGroup) {
+    const int n = L - t0 < kGroup ? L - t0 : kGroup;  // rows of this group (uniform)
+    T ypre[kGroup], fpre[kGroup], cppre[kGroup], gpre[kGroup], apre[kGroup], cabpre[kGroup];
+    int sgpre[kGroup];
 #pragma unroll
-  for (int u = 0; u < kPrefetch; ++u) {
-    const int t = t0 + u;
-    if (t >= L) break;  // uniform across the warp
-    const int l = UP ? t : (L - 1 - t);
-    T u_;
-    if (MODE == 0) {
-      u_ = ypre[u];
-    } else {
-      const T wv = ypre[u] - cppre[u] * w_prev;
-      const T wlast = w_prev;  // w of the previous row in pass order
-      w_prev = wv;
-      // ---- outgoing interface data of t^k from w^k ----
-      if (out_lane) {
+    for (int u = 0; u < kGroup; ++u) {
+      ypre[u] = ynx[u];
+      fpre[u] = f0nx[u];
+      cppre[u] = cpnx[u];
+      gpre[u] = gnx[u];
+      apre[u] = anx[u];
+      cabpre[u] = cabnx[u];
+      sgpre[u] = sgnx[u];
+    }
+    if (t0 + kGroup < L) load_group(t0 + kGroup);
+    // forcing at t^{k+1}: the first term from the prefetched row, further terms directly
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      T f = dta0 * fpre[u];
+      if (MODE != 2 && u < n)
+        for (int r = 1; r < A.nforce; ++r) {
+          const int t = t0 + u;
+          const int i = lo + (UP ? t : (L - 1 - t));
+          f += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
+        }
+      fpre[u] = f;
+    }
+
+    // (A) back-substitution chain: w^k of the group's rows
+    T wv[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (MODE != 0 && u < n) w_prev = ypre[u] - cppre[u] * w_prev;
+      wv[u] = w_prev;
+    }
+    // outgoing interface data of t^k from w^k (rows alpha / alpha-1 and beta / beta+1)
+    if (MODE != 0 && out_lane) {
+      T wlast = w_last;  // w of the previous row in pass order
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int t = t0 + u;
+        const int l = u < n ? (UP ? t : (L - 1 - t)) : -100;  // rows beyond the strip match nothing
+        const T wcur = wv[u];
         if (st.has_top) {
           const int eT = robin_ov ? (UP ? aT : aT - 1) : aT;  // the later of alpha, alpha-1
           if (l == eT) {
-            const double wa = robin_ov && !UP ? (double)wlast : (double)wv;  // w(alpha)
+            const double wa = robin_ov && !UP ? (double)wlast : (double)wcur;  // w(alpha)
             double lam;
             if (!A.robin) {
               lam = wa;
             } else if (ov >= 1) {
-              const double wb = UP ? (double)wlast : (double)wv;  // w(alpha - 1)
-              const double* zk = zcur + 0 * 2 * nxp;               // z^k at alpha, alpha-1
+              const double wb = UP ? (double)wlast : (double)wcur;  // w(alpha - 1)
+              const double* zk = zcur + 0 * 2 * nxp;                 // z^k at alpha, alpha-1
               lam = st.q_top * wa - E.inv_dt * (E.k_half * wa + E.k_off * wb - E.m_half * zk[m] - E.m_off * zk[nxp + m]);
             } else {
               lam = (st.p_top + st.q_top) * wa - A.lam_in[(((size_t)s * 2 + 0) * nt + (k - 1)) * nxp + m];
@@ -145,13 +177,13 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
         if (st.has_bot) {
           const int eB = robin_ov ? (UP ? bB + 1 : bB) : bB;  // the later of beta, beta+1
           if (l == eB) {
-            const double wbeta = robin_ov && UP ? (double)wlast : (double)wv;  // w(beta)
+            const double wbeta = robin_ov && UP ? (double)wlast : (double)wcur;  // w(beta)
             double lam;
             if (!A.robin) {
               lam = wbeta;
             } else if (ov >= 1) {
-              const double wu = UP ? (double)wv : (double)wlast;  // w(beta + 1)
-              const double* zk = zcur + 1 * 2 * nxp;              // z^k at beta, beta+1
+              const double wu = UP ? (double)wcur : (double)wlast;  // w(beta + 1)
+              const double* zk = zcur + 1 * 2 * nxp;                // z^k at beta, beta+1
               lam = st.p_bot * wbeta - E.inv_dt * (E.k_half * wbeta + E.k_off * wu - E.m_half * zk[m] - E.m_off * zk[nxp + m]);
             } else {
               lam = (st.p_bot + st.q_bot) * wbeta -
@@ -160,40 +192,59 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
             A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
           }
         }
-      }
-      // ---- transport over dt: u^k = w^k - c (w^k - w^k upstream) ----
-      const T wnb = shfl_val(wv, lane - sgpre[u]);
-      u_ = wv - cabpre[u] * (wv - wnb);
-      // ---- overlap values of u^k ----
-      if (out_lane) {
-        if (st.has_top && l >= aT && l <= aT + ov)
-          A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)u_;
-        if (st.has_bot && l >= aB && l <= aB + ov)
-          A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)u_;
-      }
-      if (MODE == 2) {
-        if (out_lane) A.UT[(size_t)(st.rowoff + l) * P + col] = u_;
-        continue;
+        wlast = wcur;
       }
     }
-    // ---- z^{k+1} = u^k + dt f^{k+1}; keep it at the trace rows for the next pass ----
-    const T z = u_ + fpre[u];
-    if (robin_ov && out_lane) {  // halo lanes hold a wrong u (their upstream lane is missing)
-      if (st.has_top && (l == aT || l == aT - 1)) znext[(size_t)(0 * 2 + (aT - l)) * nxp + m] = (double)z;
-      if (st.has_bot && (l == bB || l == bB + 1)) znext[(size_t)(1 * 2 + (l - bB)) * nxp + m] = (double)z;
+
+    // (B) transport over dt, u^k = w^k - c (w^k - w^k upstream), and z^{k+1} = u^k + dt f^{k+1}
+    T zv[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int t = t0 + u;
+      const bool ok = u < n;  // uniform
+      const int l = ok ? (UP ? t : (L - 1 - t)) : -100;
+      T uv;
+      if (MODE == 0) {
+        uv = ypre[u];
+      } else {
+        const T wnb = shfl_val(wv[u], lane - sgpre[u]);
+        uv = wv[u] - cabpre[u] * (wv[u] - wnb);
+        if (out_lane && ok) {
+          if (st.has_top && l >= aT && l <= aT + ov)
+            A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)uv;
+          if (st.has_bot && l >= aB && l <= aB + ov)
+            A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)uv;
+          if (MODE == 2) A.UT[(size_t)(st.rowoff + l) * P + col] = uv;
+        }
+      }
+      zv[u] = uv + fpre[u];
+      // z^{k+1} at the trace rows, for the next pass (halo lanes hold a wrong u: their
+      // upstream lane is missing)
+      if (MODE != 2 && robin_ov && out_lane) {
+        if (st.has_top && (l == aT || l == aT - 1)) znext[(size_t)(0 * 2 + (aT - l)) * nxp + m] = (double)zv[u];
+        if (st.has_bot && (l == bB || l == bB + 1)) znext[(size_t)(1 * 2 + (l - bB)) * nxp + m] = (double)zv[u];
+      }
     }
-    // ---- eliminate the previous row in pass order, whose right-hand side is now known ----
-    if (t >= 1) {
-      const int lp = UP ? t - 1 : L - t;
-      const T rhs = (t == 1) ? (T)(E.m_half * (double)zm1 + E.m_off * (double)z)  // end row: one element
-                             : (T)(E.m_off * (double)zm2 + E.m_full * (double)zm1 + E.m_off * (double)z);
-      eliminate(lp, rhs, g_last, a_last);
+
+    // (C) elimination of the previous row of every row of the group (its right-hand
+    //     side M z needs z of both neighbours); zm2, zm1, g_last, a_last, w_last follow
+    //     the rows in pass order
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int t = t0 + u;
+      if (u < n) {
+        if (MODE != 2 && t >= 1) {
+          const T rhs = (t == 1) ? (T)(E.m_half * (double)zm1 + E.m_off * (double)zv[u])  // end row: one element
+                                 : (T)(E.m_off * (double)zm2 + E.m_full * (double)zm1 + E.m_off * (double)zv[u]);
+          eliminate(UP ? t - 1 : L - t, rhs, g_last, a_last);
+        }
+        zm2 = zm1;
+        zm1 = zv[u];
+        g_last = gpre[u];
+        a_last = apre[u];
+        w_last = wv[u];
+      }
     }
-    zm2 = zm1;
-    zm1 = z;
-    g_last = gpre[u];
-    a_last = apre[u];
-  }
   }
   if (MODE != 2) {
     // the last row in pass order: an end row (one element)
