@@ -26,6 +26,12 @@ CASES = [
     ("random_data_dirichlet_ov3", lambda: inputs.random_data(60, 48, 8, 0.01, 3, 3, False, seed=31, nforce=1)),
     ("random_no_bc_robin_pq", lambda: inputs.random_data(90, 256, 6, 0.002, 2, 2, True, p=6.0, q=3.0, seed=32,
                                                          nforce=1, boundary_data=False)),
+    # the paper's model problem: periodic x and zero flux in v, with this library's scheme
+    # in the serial order, and with the split P1 scheme of Section 6.2
+    ("model_problem_serial_order", lambda: inputs.gaussian_bumps(96, 128, 30, 2.5e-3, 4, p=6.0, seed=7).replace(
+        neumann_v=True, periodic_x=True, gauss_seidel=True)),
+    ("model_problem_split_scheme", lambda: inputs.gaussian_bumps(96, 128, 30, 2.5e-3, 4, p=6.0, seed=7).replace(
+        neumann_v=True, periodic_x=True, scheme=1)),
 ]
 
 
