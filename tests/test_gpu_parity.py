@@ -222,13 +222,18 @@ def test_resume_from_set_traces():
         assert np.array_equal(s.error()[3], hist[2:])
 
 
-def test_tolerance_stops_and_reports():
+@pytest.mark.parametrize("factory", [inputs.small_dirichlet, inputs.small_robin], ids=["dirichlet", "robin"])
+def test_tolerance_stops_and_reports(factory):
+    """The small workload iterated until the interface change is below 1e-10 (or 50
+    iterations): the same count as the oracle, and the final iterate matches it."""
     swr = _swr()
-    prob = inputs.small_dirichlet()
+    prob = factory()
     ref = oracle.swr_solve(prob, 50, 1e-10, 0)
     with swr.SWR(prob) as s:
         n = s.sweep(50, 1e-10, 0)
-        assert n == ref["iters"]
+        assert n == ref["iters"]  # 29 (Dirichlet, overlap 4); the 50-iteration cap (Robin p = 2)
+        u = s.solution()
+        assert np.abs(u - ref["u_T"]).max() <= 1e-12 * np.abs(ref["u_T"]).max()
         with pytest.raises(swr.KfpError) as ei:
             swr.kfp_swr_sweep(s.h, 2, 1e-30, 1)
         assert ei.value.status == swr.KFP_ENOTCONV
