@@ -1,0 +1,96 @@
+"""Host-side logic that needs no GPU: the autotuner's cache, the experiment tables,
+the problem flags, the model-problem inputs and the benchmark's profile lookup."""
+import hashlib
+import json
+import types
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_1306_4596_gb300 import autotune, experiments, inputs, swr
+
+
+class _FakeBatch:
+    def __init__(self, probs):
+        self.probs = probs
+        self.configured = []
+
+    def configure(self, bps, order):
+        self.configured.append((bps, order))
+
+
+def test_autotune_signature_ignores_problem_order_but_not_precision():
+    probs = inputs.batch_instances(4)
+    a = autotune.signature(probs, "f64")
+    assert a == autotune.signature(list(reversed(probs)), "f64")
+    assert a != autotune.signature(probs, "f32")
+    assert a != autotune.signature(probs[:3], "f64")
+
+
+def test_autotune_applies_a_cached_choice_without_timing(tmp_path, monkeypatch):
+    monkeypatch.setenv("KFP_SWR_CACHE", str(tmp_path))
+    probs = inputs.batch_instances(3)
+    key = autotune.signature(probs, "f64")
+    entry = {"blocks_per_sm": 1, "unit_order": 0, "ms": 1.5, "candidates": []}
+    (tmp_path / "autotune.json").write_text(json.dumps({key: entry}))
+    fake = _FakeBatch(probs)
+    res = autotune.tune(fake, "f64")
+    assert res["cached"] and fake.configured == [(1, 0)]
+
+
+def test_table1_formatting():
+    rows = [
+        {"method": "CSWR", "overlap": 3, "j": 0, "iters": 106, "converged": True},
+        {"method": "CSWR", "overlap": 3, "j": 1, "iters": 150, "converged": False},
+        {"method": "CSWR", "overlap": 0, "j": 0, "iters": 1, "converged": False},
+        {"method": "OSWR(p)", "overlap": 0, "j": 0, "iters": 11, "converged": True},
+    ]
+    text = experiments.format_table1(rows)
+    lines = text.splitlines()
+    assert lines[0] == "| decomposition | method | j=0 | j=1 |"
+    assert "| overlap 3 cells | CSWR | 106 | >150 |" in lines
+    assert "| no overlap | CSWR | - |  |" in lines
+    assert "| no overlap | OSWR(p) | 11 |  |" in lines
+
+
+def test_problem_flags():
+    p = inputs.small_robin()
+    assert swr.problem_flags(p) == 0
+    assert swr.problem_flags(p.replace(gauss_seidel=True)) == swr.KFP_FLAG_GAUSS_SEIDEL
+    both = p.replace(neumann_v=True, periodic_x=True, scheme=1)
+    assert swr.problem_flags(both) == (swr.KFP_FLAG_NEUMANN_V | swr.KFP_FLAG_PERIODIC_X | swr.KFP_FLAG_SPLIT_SCHEME)
+
+
+@pytest.mark.parametrize("j", [0, 1])
+def test_model_error_equation_setting(j):
+    prob = inputs.model_error_equation(j, overlap=3, robin=True, p=4.23, seed=7)
+    n = 100 * 2 ** j
+    assert (prob.nx, prob.nv, prob.nt) == (n, 2 * n, 2 * n)
+    assert prob.dt == prob.hx == pytest.approx(prob.hv)
+    assert prob.neumann_v and prob.periodic_x
+    assert oracle.validate(prob) == 0  # Courant number exactly 1 at v = +-1 is accepted
+    assert np.all(prob.lam0[:, 1] == 0) and np.abs(prob.lam0[:, 0]).max() <= 1
+    again = inputs.model_error_equation(j, overlap=3, robin=True, p=4.23, seed=7)
+    assert np.array_equal(prob.lam0, again.lam0)
+    assert not np.array_equal(prob.lam0, inputs.model_error_equation(j, seed=8).lam0)
+
+
+def test_profiled_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    src = tmp_path / "kernel.cuh"
+    src.write_bytes(b"// kernel v1\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    summary = tmp_path / "summary.md"
+    summary.write_text(f"source sha256[:16] = {digest}\ntraffic_bytes_per_launch f64 = 1234\n")
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(summary))
+    monkeypatch.setattr(bench, "SWEEP_SOURCE", str(src))
+    assert bench.profiled_traffic("f64") == 1234
+    assert bench.profiled_traffic("f32") is None
+    src.write_bytes(b"// kernel v2\n")
+    assert bench.profiled_traffic("f64") is None
+
+
+def test_job_rate_and_single_rank_time():
+    assert bench.job_rate(2, 1_000, 3, 500.0) == pytest.approx(2 * 1_000 * 3 / 0.5)
+    assert bench.max_over_ranks(None, None, 1, 12.5) == 12.5
