@@ -983,10 +983,10 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   TRY(alloc(h, &h->UT, ystate));
   TRY(alloc(h, &h->U0, (size_t)(g.nv + 1) * g.P * es));
   TRY(alloc(h, &h->F, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es));
-  cudaMemsetAsync(h->Ybuf, 0, 2 * ystate, h->stream);
-  cudaMemsetAsync(h->UT, 0, ystate, h->stream);
-  cudaMemsetAsync(h->U0, 0, (size_t)(g.nv + 1) * g.P * es, h->stream);
-  cudaMemsetAsync(h->F, 0, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es, h->stream);
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->Ybuf, 0, 2 * ystate, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->UT, 0, ystate, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->U0, 0, (size_t)(g.nv + 1) * g.P * es, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->F, 0, (size_t)std::max(g.nforce, 1) * (g.nv + 1) * g.P * es, h->stream));
   TRY(upload_padded(h, pb->u0, g.nv + 1, pb->on_device, h->U0));
   for (int r = 0; r < g.nforce; ++r)
     TRY(upload_padded(h, pb->f_space + (size_t)r * (g.nv + 1) * nxp, g.nv + 1, pb->on_device,
@@ -1054,7 +1054,7 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   if (g.split) {
     const size_t nz = (size_t)2 * g.S * 2 * 2 * nxp;
     TRY(alloc(h, (void**)&h->zrec, sizeof(double) * nz));
-    cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream);
+    KFP_CUDA_TRY_H(cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream));
   } else if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
     rc = setup_tma(h, pb);
     if (rc) return rc;
@@ -1080,15 +1080,15 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   TRY(alloc(h, (void**)&h->lam_in, sizeof(double) * h->n_trace));
   TRY(alloc(h, (void**)&h->lam_next, sizeof(double) * h->n_trace));
   TRY(alloc(h, (void**)&h->bands, sizeof(double) * h->n_band));
-  cudaMemsetAsync(h->lam_next, 0, sizeof(double) * h->n_trace, h->stream);
-  cudaMemsetAsync(h->bands, 0, sizeof(double) * h->n_band, h->stream);
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->lam_next, 0, sizeof(double) * h->n_trace, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->bands, 0, sizeof(double) * h->n_band, h->stream));
   if (pb->lambda0) TRY(copy_in(h, h->lam_in, pb->lambda0, sizeof(double) * h->n_trace, pb->on_device));
-  else cudaMemsetAsync(h->lam_in, 0, sizeof(double) * h->n_trace, h->stream);
+  else KFP_CUDA_TRY_H(cudaMemsetAsync(h->lam_in, 0, sizeof(double) * h->n_trace, h->stream));
   TRY(wrap_traces(h, h->lam_in));
 
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  KFP_CUDA_TRY_H(cudaGetDevice(&dev));
+  KFP_CUDA_TRY_H(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   h->device = dev;
   h->reduce_blocks = std::max(sms, 1) * 4;
   TRY(alloc(h, (void**)&h->partial, sizeof(double) * 4 * h->reduce_blocks));
@@ -1096,9 +1096,9 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   TRY(alloc(h, (void**)&h->scal, sizeof(double) * 3));
   TRY(alloc(h, (void**)&h->iter, sizeof(int)));
   TRY(alloc(h, (void**)&h->stage, sizeof(double) * (g.nv + 1) * nxp));
-  cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * 2, h->stream);
-  cudaMemsetAsync(h->scal, 0, sizeof(double) * 3, h->stream);
-  cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream);
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned) * 2, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->scal, 0, sizeof(double) * 3, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream));
   KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->host_scal, sizeof(double) * 3));
   for (auto& e : h->ev) KFP_CUDA_TRY_H(cudaEventCreate(&e));
   KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
@@ -1748,10 +1748,13 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
   }
   if (!rc) {
     int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || b->sms < 1) {
+      cudaGetLastError();
+      rc = b->fail(KFP_ECUDA, "querying the device failed");
+    }
     for (auto& e : b->ev)
-      if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = KFP_ECUDA;
+      if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = b->fail(KFP_ECUDA, "cudaEventCreate failed");
     if (!rc) rc = b->prec == KFP_F64 ? batch_setup<double>(b) : batch_setup<float>(b);
     if (rc) g_batch_create_error = b->last_error;
   }
