@@ -21,9 +21,16 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "kfp_kernels.cuh"
 
 namespace kfp {
+
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
 
 struct FeArgs {
   double m_full, m_half, m_off;  // P1 mass matrix entries: 2h/3, h/3 (end node), h/6
@@ -77,7 +84,9 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   T w_prev = T(0), y_prev = T(0), zm1 = T(0), zm2 = T(0);
   T g_last = T(0), a_last = T(0);  // factors of the previous row in pass order
   T w_last = T(0);                 // w of the previous row in pass order
-  // elimination of local row l from the M-weighted right-hand side rhs
+  const T mo = (T)E.m_off, mf = (T)E.m_full, mh = (T)E.m_half;
+  // elimination of local row l from the M-weighted right-hand side rhs (end rows
+  // take the interface data)
   auto eliminate = [&](int l, T rhs, T gl, T al) {
     const bool top_end = l == L - 1, bot_end = l == 0;
     T R = rhs;
@@ -88,6 +97,21 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
     y_prev = y;
   };
 
+  // Element t of the pass is local row l(t) = t (UP) or L-1-t; the per-row tables
+  // and grid rows of l(t) are addressed from the row of t = 0 in steps of dl or dP.
+  constexpr int dl = UP ? 1 : -1;
+  const int l_first = UP ? 0 : L - 1;
+  const ptrdiff_t dP = (ptrdiff_t)dl * P;
+  const T* __restrict__ gEt = gE + l_first;
+  const T* __restrict__ aEt = aE + l_first;
+  const T* __restrict__ cpt = cpB + l_first;
+  const T* __restrict__ cabt = A.cabs + lo + l_first;
+  const signed char* __restrict__ sgt = A.sgn + lo + l_first;
+  const T* __restrict__ yt =
+      (MODE == 0 ? A.U0 + (size_t)(lo + l_first) * P : Ycur + (size_t)(st.rowoff + l_first) * P) + col;
+  const T* __restrict__ ft = A.F + (size_t)(lo + l_first) * P + col;
+  T* __restrict__ ynt = Ynext + (size_t)(st.rowoff + l_first) * P + col;
+
   // Rows go in groups of kGroup.  The inputs of the next group are loaded while the
   // current one is computed (two register buffers), then per group: (A) the
   // back-substitution chain, (B) the transport, z and the overlap values of every row
@@ -96,61 +120,60 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   constexpr int kGroup = 4;
   T ynx[kGroup], f0nx[kGroup], cpnx[kGroup], gnx[kGroup], anx[kGroup], cabnx[kGroup];
   int sgnx[kGroup];
-  const T dta0 = (MODE != 2 && A.nforce > 0) ? (T)A.dta[(size_t)k1 * A.nforce] : T(0);
+  const bool force0 = MODE != 2 && A.nforce > 0;
+  const T dta0 = force0 ? (T)A.dta[(size_t)k1 * A.nforce] : T(0);
   auto load_group = [&](int tb) {
+    if (tb + kGroup <= L) {  // uniform: a whole group inside the strip
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
-      const int t = tb + u;
-      const bool ok = t < L;
-      const int l = ok ? (UP ? t : (L - 1 - t)) : 0;
-      const int i = lo + l;
-      ynx[u] = !ok ? T(0) : (MODE == 0 ? A.U0[(size_t)i * P + col] : Ycur[(size_t)(st.rowoff + l) * P + col]);
-      f0nx[u] = (MODE != 2 && ok && A.nforce > 0) ? A.F[(size_t)i * P + col] : T(0);
-      cpnx[u] = ok ? cpB[l] : T(0);
-      gnx[u] = ok ? gE[l] : T(0);
-      anx[u] = ok ? aE[l] : T(0);
-      cabnx[u] = ok ? A.cabs[i] : T(0);
-      sgnx[u] = ok ? A.sgn[i] : 0;
+      for (int u = 0; u < kGroup; ++u) {
+        const int t = tb + u;
+        ynx[u] = yt[dP * t];
+        f0nx[u] = force0 ? ft[dP * t] : T(0);
+        cpnx[u] = cpt[dl * t];
+        gnx[u] = gEt[dl * t];
+        anx[u] = aEt[dl * t];
+        cabnx[u] = cabt[dl * t];
+        sgnx[u] = sgt[dl * t];
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int t = tb + u;
+        const bool ok = t < L;
+        ynx[u] = ok ? yt[dP * t] : T(0);
+        f0nx[u] = (force0 && ok) ? ft[dP * t] : T(0);
+        cpnx[u] = ok ? cpt[dl * t] : T(0);
+        gnx[u] = ok ? gEt[dl * t] : T(0);
+        anx[u] = ok ? aEt[dl * t] : T(0);
+        cabnx[u] = ok ? cabt[dl * t] : T(0);
+        sgnx[u] = ok ? sgt[dl * t] : 0;
+      }
     }
   };
-  load_group(0);
-  for (int t0 = 0; t0 < L; t0 += kGroup) {
-    const int n = L - t0 < kGroup ? L - t0 : kGroup;  // rows of this group (uniform)
-    T ypre[kGroup], fpre[kGroup], cppre[kGroup], gpre[kGroup], apre[kGroup], cabpre[kGroup];
-    int sgpre[kGroup];
-#pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
-      ypre[u] = ynx[u];
-      fpre[u] = f0nx[u];
-      cppre[u] = cpnx[u];
-      gpre[u] = gnx[u];
-      apre[u] = anx[u];
-      cabpre[u] = cabnx[u];
-      sgpre[u] = sgnx[u];
-    }
-    if (t0 + kGroup < L) load_group(t0 + kGroup);
-    // forcing at t^{k+1}: the first term from the prefetched row, further terms directly
-#pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
-      T f = dta0 * fpre[u];
-      if (MODE != 2 && u < n)
-        for (int r = 1; r < A.nforce; ++r) {
-          const int t = t0 + u;
-          const int i = lo + (UP ? t : (L - 1 - t));
-          f += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + i) * P + col];
-        }
-      fpre[u] = f;
-    }
 
+  // Groups whose rows (and the row before them, which they eliminate) are neither a
+  // strip end nor a row of the outgoing data (traces, overlap values, z records) take
+  // the plain path.  Rows [ls0, ls1] are such rows; a group starting at t0 touches
+  // the rows of t0-1 .. t0+kGroup-1.
+  int ls0 = 1, ls1 = L - 2;
+  if (st.has_bot) ls0 = max(ls0, max(aB + ov, bB + 1) + 1);
+  if (st.has_top) ls1 = min(ls1, aT - 2);
+  const int t_plain0 = UP ? ls0 + 1 : L - ls1;
+  const int t_plain1 = UP ? ls1 - kGroup + 1 : L - kGroup - ls0;
+
+  T ypre[kGroup], fpre[kGroup], cppre[kGroup], gpre[kGroup], apre[kGroup], cabpre[kGroup];
+  int sgpre[kGroup];
+  auto run_group = [&](auto plain_tag, const int t0, const int n) {
+    constexpr bool PLAIN = decltype(plain_tag)::value;
     // (A) back-substitution chain: w^k of the group's rows
     T wv[kGroup];
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
-      if (MODE != 0 && u < n) w_prev = ypre[u] - cppre[u] * w_prev;
+      if (MODE != 0 && (PLAIN || u < n)) w_prev = ypre[u] - cppre[u] * w_prev;
       wv[u] = w_prev;
     }
     // outgoing interface data of t^k from w^k (rows alpha / alpha-1 and beta / beta+1)
-    if (MODE != 0 && out_lane) {
+    if (!PLAIN && MODE != 0 && out_lane) {
       T wlast = w_last;  // w of the previous row in pass order
 #pragma unroll
       for (int u = 0; u < kGroup; ++u) {
@@ -201,7 +224,7 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       const int t = t0 + u;
-      const bool ok = u < n;  // uniform
+      const bool ok = PLAIN || u < n;  // uniform
       const int l = ok ? (UP ? t : (L - 1 - t)) : -100;
       T uv;
       if (MODE == 0) {
@@ -209,18 +232,23 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
       } else {
         const T wnb = shfl_val(wv[u], lane - sgpre[u]);
         uv = wv[u] - cabpre[u] * (wv[u] - wnb);
-        if (out_lane && ok) {
+        if (!PLAIN && out_lane && ok) {
           if (st.has_top && l >= aT && l <= aT + ov)
             A.bands[((((size_t)s * 2 + 0) * nt + (k - 1)) * (ov + 1) + (l - aT)) * nxp + m] = (double)uv;
           if (st.has_bot && l >= aB && l <= aB + ov)
             A.bands[((((size_t)(s - 1) * 2 + 1) * nt + (k - 1)) * (ov + 1) + (l - aB)) * nxp + m] = (double)uv;
-          if (MODE == 2) A.UT[(size_t)(st.rowoff + l) * P + col] = uv;
         }
+        if (MODE == 2 && out_lane && ok) A.UT[(size_t)(st.rowoff + l) * P + col] = uv;
       }
-      zv[u] = uv + fpre[u];
+      // forcing at t^{k+1}: the first term from the prefetched row, further terms directly
+      T z = fma(dta0, fpre[u], uv);
+      if (MODE != 2 && ok)
+        for (int r = 1; r < A.nforce; ++r)
+          z += (T)A.dta[(size_t)k1 * A.nforce + r] * A.F[((size_t)r * (A.nv + 1) + lo + l) * P + col];
+      zv[u] = z;
       // z^{k+1} at the trace rows, for the next pass (halo lanes hold a wrong u: their
       // upstream lane is missing)
-      if (MODE != 2 && robin_ov && out_lane) {
+      if (!PLAIN && MODE != 2 && robin_ov && out_lane) {
         if (st.has_top && (l == aT || l == aT - 1)) znext[(size_t)(0 * 2 + (aT - l)) * nxp + m] = (double)zv[u];
         if (st.has_bot && (l == bB || l == bB + 1)) znext[(size_t)(1 * 2 + (l - bB)) * nxp + m] = (double)zv[u];
       }
@@ -232,10 +260,14 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       const int t = t0 + u;
-      if (u < n) {
-        if (MODE != 2 && t >= 1) {
-          const T rhs = (t == 1) ? (T)(E.m_half * (double)zm1 + E.m_off * (double)zv[u])  // end row: one element
-                                 : (T)(E.m_off * (double)zm2 + E.m_full * (double)zm1 + E.m_off * (double)zv[u]);
+      if (PLAIN || u < n) {
+        if (MODE != 2 && PLAIN) {  // an interior row: three elements, no interface data
+          const T y = g_last * ((mo * zm2 + mf * zm1 + mo * zv[u]) - a_last * y_prev);
+          if (out_lane) ynt[dP * (t - 1)] = y;
+          y_prev = y;
+        } else if (MODE != 2 && t >= 1) {
+          const T rhs = (t == 1) ? mh * zm1 + mo * zv[u]  // end row: one element
+                                 : mo * zm2 + mf * zm1 + mo * zv[u];
           eliminate(UP ? t - 1 : L - t, rhs, g_last, a_last);
         }
         zm2 = zm1;
@@ -245,10 +277,28 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
         w_last = wv[u];
       }
     }
+  };
+
+  load_group(0);
+  for (int t0 = 0; t0 < L; t0 += kGroup) {
+    const int n = L - t0 < kGroup ? L - t0 : kGroup;  // rows of this group (uniform)
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      ypre[u] = ynx[u];
+      fpre[u] = f0nx[u];
+      cppre[u] = cpnx[u];
+      gpre[u] = gnx[u];
+      apre[u] = anx[u];
+      cabpre[u] = cabnx[u];
+      sgpre[u] = sgnx[u];
+    }
+    if (t0 + kGroup < L) load_group(t0 + kGroup);
+    if (t0 >= t_plain0 && t0 <= t_plain1) run_group(BoolTag<true>{}, t0, kGroup);
+    else run_group(BoolTag<false>{}, t0, n);
   }
   if (MODE != 2) {
     // the last row in pass order: an end row (one element)
-    const T rhs = (L == 1) ? (T)(E.m_half * (double)zm1) : (T)(E.m_half * (double)zm1 + E.m_off * (double)zm2);
+    const T rhs = (L == 1) ? mh * zm1 : mh * zm1 + mo * zm2;
     eliminate(UP ? L - 1 : 0, rhs, g_last, a_last);
   }
 }
