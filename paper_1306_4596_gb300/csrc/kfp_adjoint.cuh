@@ -103,86 +103,133 @@ adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
   }
 
   double w_prev = 0.0, y_prev = 0.0;
-  // rows go in groups of kPrefetch whose residues are loaded together, so that the
+  // Row l(t) = t (UP) or L-1-t of the pass; its table entries and residue rows are
+  // addressed from the row of t = 0 in steps of dl or dP.
+  constexpr int dl = UP ? 1 : -1;
+  const int l_first = UP ? 0 : L - 1;
+  const ptrdiff_t dP = (ptrdiff_t)dl * P;
+  const double* __restrict__ gEt = gE + l_first;
+  const double* __restrict__ aEt = aE + l_first;
+  const double* __restrict__ cpt = cpB + l_first;
+  const double* __restrict__ cabt = A.cabs + lo + l_first;
+  const signed char* __restrict__ sgt = A.sgn + lo + l_first;
+  const double* __restrict__ yt = Ycur + (size_t)(st.rowoff + l_first) * P + col;
+  double* __restrict__ ynt = Ynext + (size_t)(st.rowoff + l_first) * P + col;
+  // Away from v = v0, v1 a row (i, m) is an identity row only at an inflow column, so
+  // whether the transposed upwind term takes w of this column (a) and of the
+  // downstream column m + sg (b) depends on the lane and the sign of v alone.
+  const bool a_pos = m != 0, a_neg = m != A.nx;
+  const bool b_pos = m >= 0 && m <= A.nx - 1, b_neg = m >= 1 && m <= A.nx;
+
+  // rows go in groups of kPrefetch whose inputs are loaded together, so that the
   // loads of a group are in flight at once instead of one latency per row
   // (the inputs of the next group are loaded while the current one is computed)
   constexpr int kPrefetch = 4;
   double ynx[kPrefetch], cnx[kPrefetch], gnx[kPrefetch], anx[kPrefetch], cabnx[kPrefetch];
   int sgnx[kPrefetch];
   auto load_group = [&](int tb) {
+    if (tb + kPrefetch <= L) {  // uniform: a whole group inside the strip
 #pragma unroll
-    for (int u = 0; u < kPrefetch; ++u) {
-      const int t = tb + u;
-      const bool ok = t < L;
-      const int l = ok ? (UP ? t : (L - 1 - t)) : 0;
-      ynx[u] = (MODE != 0 && ok) ? Ycur[(size_t)(st.rowoff + l) * P + col] : 0.0;
-      cnx[u] = ok ? cpB[l] : 0.0;
-      gnx[u] = ok ? gE[l] : 0.0;
-      anx[u] = ok ? aE[l] : 0.0;
-      cabnx[u] = ok ? A.cabs[lo + l] : 0.0;
-      sgnx[u] = ok ? A.sgn[lo + l] : 0;
+      for (int u = 0; u < kPrefetch; ++u) {
+        const int t = tb + u;
+        ynx[u] = MODE != 0 ? yt[dP * t] : 0.0;
+        cnx[u] = cpt[dl * t];
+        gnx[u] = gEt[dl * t];
+        anx[u] = aEt[dl * t];
+        cabnx[u] = cabt[dl * t];
+        sgnx[u] = sgt[dl * t];
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < kPrefetch; ++u) {
+        const int t = tb + u;
+        const bool ok = t < L;
+        ynx[u] = (MODE != 0 && ok) ? yt[dP * t] : 0.0;
+        cnx[u] = ok ? cpt[dl * t] : 0.0;
+        gnx[u] = ok ? gEt[dl * t] : 0.0;
+        anx[u] = ok ? aEt[dl * t] : 0.0;
+        cabnx[u] = ok ? cabt[dl * t] : 0.0;
+        sgnx[u] = ok ? sgt[dl * t] : 0;
+      }
     }
   };
-  load_group(0);
-  for (int t0 = 0; t0 < L; t0 += kPrefetch) {
+
   double ypre[kPrefetch], cpre[kPrefetch], gpre[kPrefetch], apre[kPrefetch], cabpre[kPrefetch];
   int sgpre[kPrefetch];
+  // Groups of rows 1 .. L-2 only (no interface row, no v boundary) take the plain
+  // path: no interface terms and no identity-row tests per row.
+  auto run_group = [&](auto plain_tag, const int t0) {
+    constexpr bool PLAIN = decltype(plain_tag)::value;
 #pragma unroll
-  for (int u = 0; u < kPrefetch; ++u) {
-    ypre[u] = ynx[u]; cpre[u] = cnx[u]; gpre[u] = gnx[u]; apre[u] = anx[u]; cabpre[u] = cabnx[u]; sgpre[u] = sgnx[u];
-  }
-  if (t0 + kPrefetch < L) load_group(t0 + kPrefetch);
-#pragma unroll
-  for (int u = 0; u < kPrefetch; ++u) {
-    const int t = t0 + u;
-    if (t >= L) break;  // uniform across the warp
-    const int l = UP ? t : (L - 1 - t);
-    const int i = lo + l;
-    double wv = 0.0;  // w^{le+1} (zero beyond nt)
-    if (MODE != 0) {
-      wv = ypre[u] - cpre[u] * w_prev;
-      w_prev = wv;
-      // ---- adjoint of the consumed data and the gradient terms at level lb ----
-      if (out_lane) {
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int t = t0 + u;
+      if (!PLAIN && t >= L) break;  // uniform across the warp
+      const int l = UP ? t : (L - 1 - t);
+      const int i = lo + l;
+      double wv = 0.0;  // w^{le+1} (zero beyond nt)
+      if (MODE != 0) {
+        wv = ypre[u] - cpre[u] * w_prev;
+        w_prev = wv;
+        // ---- adjoint of the consumed data and the gradient terms at level lb ----
+        if (!PLAIN && out_lane) {
+          if (st.has_top && l == L - 1) {
+            const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
+            const size_t at = (size_t)(lb - 1) * nxp + m;
+            A.lbar_in[((size_t)s * 2 + 0) * tr + at] = A.two_dt_hv * wr - lbo_b_top;
+            A.contrib[((size_t)s * 4 + 0) * tr + at] += -A.two_dt_hv * wr * ub_top + lbo_b_top * ub_top;
+            A.contrib[((size_t)s * 4 + 1) * tr + at] += lbo_b_top * ub_top;
+          }
+          if (st.has_bot && l == 0) {
+            const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
+            const size_t at = (size_t)(lb - 1) * nxp + m;
+            A.lbar_in[((size_t)(s - 1) * 2 + 1) * tr + at] = A.two_dt_hv * wr - lbo_b_bot;
+            A.contrib[((size_t)(s - 1) * 4 + 3) * tr + at] += -A.two_dt_hv * wr * ub_bot + lbo_b_bot * ub_bot;
+            A.contrib[((size_t)(s - 1) * 4 + 2) * tr + at] += lbo_b_bot * ub_bot;
+          }
+        }
+        if (MODE == 2) continue;
+      }
+      // ---- right-hand side of level le: E^T w^{le+1} + sources, then elimination ----
+      const int sg = sgpre[u];
+      const double wdn = shfl_val(wv, lane + sg);  // w^{le+1} of the downstream column
+      const double c = cabpre[u];
+      double mu = 0.0;
+      if (PLAIN) {
+        if (MODE != 0) {  // (1 - c) a + c b as a + c (b - a)
+          const double a = (sg > 0 ? a_pos : (sg < 0 ? a_neg : true)) ? wv : 0.0;
+          const double b = (sg > 0 ? b_pos : (sg < 0 ? b_neg : false)) ? wdn : 0.0;
+          mu = a + c * (b - a);
+        }
+      } else {
+        if (MODE != 0) {
+          if (!adj_identity(A, i, m, sg)) mu += (1.0 - c) * wv;
+          const int md = m + sg;
+          if (sg != 0 && md >= 0 && md <= A.nx && !adj_identity(A, i, md, sg)) mu += c * wdn;
+        }
         if (st.has_top && l == L - 1) {
-          const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
-          const size_t at = (size_t)(lb - 1) * nxp + m;
-          A.lbar_in[((size_t)s * 2 + 0) * tr + at] = A.two_dt_hv * wr - lbo_b_top;
-          A.contrib[((size_t)s * 4 + 0) * tr + at] += -A.two_dt_hv * wr * ub_top + lbo_b_top * ub_top;
-          A.contrib[((size_t)s * 4 + 1) * tr + at] += lbo_b_top * ub_top;
+          if (last_iterate) mu += 2.0 * A.dthx * (ue_top - ue_top_o);
+          mu += (st.p_top + st.q_top) * lbo_e_top;
         }
         if (st.has_bot && l == 0) {
-          const double wr = adj_identity(A, i, m, sgpre[u]) ? 0.0 : wv;
-          const size_t at = (size_t)(lb - 1) * nxp + m;
-          A.lbar_in[((size_t)(s - 1) * 2 + 1) * tr + at] = A.two_dt_hv * wr - lbo_b_bot;
-          A.contrib[((size_t)(s - 1) * 4 + 3) * tr + at] += -A.two_dt_hv * wr * ub_bot + lbo_b_bot * ub_bot;
-          A.contrib[((size_t)(s - 1) * 4 + 2) * tr + at] += lbo_b_bot * ub_bot;
+          if (last_iterate) mu += -2.0 * A.dthx * (ue_bot_o - ue_bot);
+          mu += (st.p_bot + st.q_bot) * lbo_e_bot;
         }
       }
-      if (MODE == 2) continue;
+      const double y = gpre[u] * (mu - apre[u] * y_prev);
+      if (out_lane) ynt[dP * t] = y;
+      y_prev = y;
     }
-    // ---- right-hand side of level le: E^T w^{le+1} + sources, then elimination ----
-    const int sg = sgpre[u];
-    const double wdn = shfl_val(wv, lane + sg);  // w^{le+1} of the downstream column
-    const double c = cabpre[u];
-    double mu = 0.0;
-    if (MODE != 0) {
-      if (!adj_identity(A, i, m, sg)) mu += (1.0 - c) * wv;
-      const int md = m + sg;
-      if (sg != 0 && md >= 0 && md <= A.nx && !adj_identity(A, i, md, sg)) mu += c * wdn;
+  };
+
+  load_group(0);
+  for (int t0 = 0; t0 < L; t0 += kPrefetch) {
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      ypre[u] = ynx[u]; cpre[u] = cnx[u]; gpre[u] = gnx[u]; apre[u] = anx[u]; cabpre[u] = cabnx[u]; sgpre[u] = sgnx[u];
     }
-    if (st.has_top && l == L - 1) {
-      if (last_iterate) mu += 2.0 * A.dthx * (ue_top - ue_top_o);
-      mu += (st.p_top + st.q_top) * lbo_e_top;
-    }
-    if (st.has_bot && l == 0) {
-      if (last_iterate) mu += -2.0 * A.dthx * (ue_bot_o - ue_bot);
-      mu += (st.p_bot + st.q_bot) * lbo_e_bot;
-    }
-    const double y = gpre[u] * (mu - apre[u] * y_prev);
-    if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
-    y_prev = y;
-  }
+    if (t0 + kPrefetch < L) load_group(t0 + kPrefetch);
+    if (t0 >= 1 && t0 + kPrefetch <= L - 1) run_group(BoolTag<true>{}, t0);
+    else run_group(BoolTag<false>{}, t0);
   }
 }
 

@@ -27,11 +27,6 @@
 
 namespace kfp {
 
-template <bool B>
-struct BoolTag {
-  static constexpr bool value = B;
-};
-
 struct FeArgs {
   double m_full, m_half, m_off;  // P1 mass matrix entries: 2h/3, h/3 (end node), h/6
   double k_half, k_off;          // (M + dt S) entries of an end row: h/3 + dt/h, h/6 - dt/h

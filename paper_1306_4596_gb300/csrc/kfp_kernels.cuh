@@ -29,6 +29,7 @@
 // deterministic last-block final reduction.
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace kfp {
@@ -69,6 +70,12 @@ struct PassArgs {
   T* Y0;                       // [rows][P] elimination residue, even steps
   T* Y1;                       // odd steps
   T* UT;                       // [rows][P] state at t = T
+};
+
+// compile-time flag for a generic lambda instantiated on two code paths
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
 };
 
 __device__ __forceinline__ double shfl_val(double v, int src) {
