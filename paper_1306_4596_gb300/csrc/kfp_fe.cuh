@@ -31,7 +31,10 @@ struct FeArgs {
   double m_full, m_half, m_off;  // P1 mass matrix entries: 2h/3, h/3 (end node), h/6
   double k_half, k_off;          // (M + dt S) entries of an end row: h/3 + dt/h, h/6 - dt/h
   double dt, inv_dt;
+  double dt_mo, inv_mo;          // dt / m_off, 1 / m_off
   double* zrec;                  // [2 parities][S][2 ends][2 rows][nx+1] z^k at the trace rows
+  const void* tab;               // [S][2 directions][2][Lmax] of T: g m_off, g a (elimination
+                                 // of a right-hand side in units of m_off)
 };
 
 template <typename T, bool UP, int MODE>
@@ -49,9 +52,11 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   const int L = st.L, lo = st.lo, P = A.P, nxp = A.nx + 1, nt = A.nt;
   const int dirE = UP ? 0 : 1;
   const int dirB = UP ? 1 : 0;
-  // periodic x: every column has the same factors (class 1)
-  const T* __restrict__ gE = A.coef + ((size_t)((s * 3 + 1) * 2 + dirE) * 3 + 0) * A.Lmax;
-  const T* __restrict__ aE = A.coef + ((size_t)((s * 3 + 1) * 2 + dirE) * 3 + 1) * A.Lmax;
+  // periodic x: every column has the same factors (class 1); the elimination takes
+  // g m_off and g a, with right-hand sides M z / m_off = z_{l-1} + 4 z_l + z_{l+1}
+  // (an end row: 2 z_l + z_neighbour)
+  const T* __restrict__ gE = (const T*)E.tab + ((size_t)s * 2 + dirE) * 2 * A.Lmax;
+  const T* __restrict__ aE = gE + A.Lmax;
   const T* __restrict__ cpB = A.coef + ((size_t)((s * 3 + 1) * 2 + dirB) * 3 + 2) * A.Lmax;
   const T* __restrict__ Ycur = (k & 1) ? A.Y1 : A.Y0;
   T* __restrict__ Ynext = ((k + 1) & 1) ? A.Y1 : A.Y0;
@@ -79,15 +84,17 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   T w_prev = T(0), y_prev = T(0), zm1 = T(0), zm2 = T(0);
   T g_last = T(0), a_last = T(0);  // factors of the previous row in pass order
   T w_last = T(0);                 // w of the previous row in pass order
-  const T mo = (T)E.m_off, mf = (T)E.m_full, mh = (T)E.m_half;
-  // elimination of local row l from the M-weighted right-hand side rhs (end rows
-  // take the interface data)
+  // elimination of local row l from the right-hand side rhs = (M z)_l / m_off, with
+  // gl = g_l m_off and al = g_l a_l (end rows take the interface data: a Robin row adds
+  // dt lambda to M z, a Dirichlet row is w = lambda)
   auto eliminate = [&](int l, T rhs, T gl, T al) {
     const bool top_end = l == L - 1, bot_end = l == 0;
     T R = rhs;
-    if (top_end && st.has_top) R = A.robin ? (T)((double)R + E.dt * lam_rhs_top) : (T)lam_rhs_top;
-    if (bot_end && st.has_bot) R = A.robin ? (T)((double)R + E.dt * lam_rhs_bot) : (T)lam_rhs_bot;
-    const T y = gl * (R - al * y_prev);
+    if (top_end && st.has_top)
+      R = A.robin ? (T)((double)R + E.dt_mo * lam_rhs_top) : (T)(lam_rhs_top * E.inv_mo);
+    if (bot_end && st.has_bot)
+      R = A.robin ? (T)((double)R + E.dt_mo * lam_rhs_bot) : (T)(lam_rhs_bot * E.inv_mo);
+    const T y = fma(-al, y_prev, gl * R);
     if (out_lane) Ynext[(size_t)(st.rowoff + l) * P + col] = y;
     y_prev = y;
   };
@@ -257,12 +264,12 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
       const int t = t0 + u;
       if (PLAIN || u < n) {
         if (MODE != 2 && PLAIN) {  // an interior row: three elements, no interface data
-          const T y = g_last * ((mo * zm2 + mf * zm1 + mo * zv[u]) - a_last * y_prev);
+          const T y = fma(-a_last, y_prev, g_last * fma(T(4), zm1, zm2 + zv[u]));
           if (out_lane) ynt[dP * (t - 1)] = y;
           y_prev = y;
         } else if (MODE != 2 && t >= 1) {
-          const T rhs = (t == 1) ? mh * zm1 + mo * zv[u]  // end row: one element
-                                 : mo * zm2 + mf * zm1 + mo * zv[u];
+          const T rhs = (t == 1) ? fma(T(2), zm1, zv[u])  // end row: one element
+                                 : fma(T(4), zm1, zm2 + zv[u]);
           eliminate(UP ? t - 1 : L - t, rhs, g_last, a_last);
         }
         zm2 = zm1;
@@ -293,7 +300,7 @@ fe_pass_kernel(const PassArgs<T> A, const FeArgs E, const int k) {
   }
   if (MODE != 2) {
     // the last row in pass order: an end row (one element)
-    const T rhs = (L == 1) ? mh * zm1 : mh * zm1 + mo * zm2;
+    const T rhs = (L == 1) ? T(2) * zm1 : fma(T(2), zm1, zm2);
     eliminate(UP ? L - 1 : 0, rhs, g_last, a_last);
   }
 }

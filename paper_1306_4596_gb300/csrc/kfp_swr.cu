@@ -266,6 +266,7 @@ struct kfp_swr {
   double* lam_next = nullptr;
   double* bands = nullptr;
   double* zrec = nullptr;      // split scheme: z^k at the trace rows, [2][S][2][2][nx+1]
+  void* fe_tab = nullptr;      // split scheme: [S][2 directions][2][Lmax] g m_off, g a (T)
   double* partial = nullptr;   // 2 doubles per reduction block
   unsigned* tickets = nullptr; // [2]
   double* scal = nullptr;      // [3] e_mis, e_chg, j_l2
@@ -416,7 +417,10 @@ struct kfp_swr {
     E.k_off = h / 6.0 - g.dt / h;
     E.dt = g.dt;
     E.inv_dt = 1.0 / g.dt;
+    E.dt_mo = g.dt / E.m_off;
+    E.inv_mo = 1.0 / E.m_off;
     E.zrec = zrec;
+    E.tab = fe_tab;
     return E;
   }
 
@@ -737,7 +741,7 @@ struct kfp_swr {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
-                    lam_in, lam_next, bands, zrec, partial, tickets, scal, hist, iter, stage, d_res,
+                    lam_in, lam_next, bands, zrec, fe_tab, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
     for (void* b : bufs)
       if (b) cudaFree(b);
@@ -1055,6 +1059,28 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
     const size_t nz = (size_t)2 * g.S * 2 * 2 * nxp;
     TRY(alloc(h, (void**)&h->zrec, sizeof(double) * nz));
     KFP_CUDA_TRY_H(cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream));
+    // elimination factors scaled for a right-hand side in units of m_off = hv/6:
+    // y_l = (g_l m_off) (M z)_l / m_off - (g_l a_l) y_{l-1} (periodic x: class 1 only)
+    const std::vector<double> coef = build_factors(g);
+    std::vector<double> tab((size_t)g.S * 2 * 2 * g.Lmax, 0.0);
+    const double m_off = g.hv / 6.0;
+    for (int s = 0; s < g.S; ++s)
+      for (int d = 0; d < 2; ++d) {
+        const double* gf = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 0) * g.Lmax];
+        const double* af = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 1) * g.Lmax];
+        double* t = &tab[(((size_t)s * 2 + d) * 2) * g.Lmax];
+        for (int l = 0; l < g.strips[s].L; ++l) {
+          t[l] = gf[l] * m_off;
+          t[g.Lmax + l] = gf[l] * af[l];
+        }
+      }
+    TRY(alloc(h, &h->fe_tab, tab.size() * es));
+    if (h->prec == KFP_F64) {
+      KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+    } else {
+      const std::vector<float> t32(tab.begin(), tab.end());
+      KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    }
   } else if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
     rc = setup_tma(h, pb);
     if (rc) return rc;
