@@ -28,7 +28,7 @@
 namespace kfp {
 
 struct FeArgs {
-  double m_full, m_half, m_off;  // P1 mass matrix entries: 2h/3, h/3 (end node), h/6
+  double m_half, m_off;          // P1 mass matrix entries: h/3 (end node), h/6 (interior: 4 m_off)
   double k_half, k_off;          // (M + dt S) entries of an end row: h/3 + dt/h, h/6 - dt/h
   double dt, inv_dt;
   double dt_mo, inv_mo;          // dt / m_off, 1 / m_off

@@ -410,7 +410,6 @@ struct kfp_swr {
   kfp::FeArgs fe_args() const {
     kfp::FeArgs E;
     const double h = g.hv;
-    E.m_full = 2.0 * h / 3.0;
     E.m_half = h / 3.0;
     E.m_off = h / 6.0;
     E.k_half = h / 3.0 + g.dt / h;
