@@ -968,6 +968,34 @@ kfp_status setup_tma(kfp_swr* h, const kfp_swr_problem* pb) {
   return h->prec == KFP_F64 ? setup_tma_t<double>(h, pb) : setup_tma_t<float>(h, pb);
 }
 
+// Split scheme: the elimination factors scaled for a right-hand side in units of
+// m_off = hv/6, [S][2 directions][2][Lmax]:
+//   y_l = (g_l m_off) (M z)_l / m_off - (g_l a_l) y_{l-1}   (periodic x: class 1 only),
+// written in the handle's precision.  Built from the current LU factors COEF, so a
+// new Robin parameter reaches the elimination as well as the back-substitution.
+kfp_status upload_fe_tab(kfp_swr* h, const std::vector<double>& coef) {
+  const Geometry& g = h->g;
+  std::vector<double> tab((size_t)g.S * 2 * 2 * g.Lmax, 0.0);
+  const double m_off = g.hv / 6.0;
+  for (int s = 0; s < g.S; ++s)
+    for (int d = 0; d < 2; ++d) {
+      const double* gf = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 0) * g.Lmax];
+      const double* af = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 1) * g.Lmax];
+      double* t = &tab[(((size_t)s * 2 + d) * 2) * g.Lmax];
+      for (int l = 0; l < g.strips[s].L; ++l) {
+        t[l] = gf[l] * m_off;
+        t[g.Lmax + l] = gf[l] * af[l];
+      }
+    }
+  if (h->prec == KFP_F64) {
+    KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+  } else {
+    const std::vector<float> t32(tab.begin(), tab.end());
+    KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+  }
+  return KFP_OK;
+}
+
 kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem* pb) {
   Geometry& g = h->g;
   const size_t es = h->elem();
@@ -1058,28 +1086,8 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
     const size_t nz = (size_t)2 * g.S * 2 * 2 * nxp;
     TRY(alloc(h, (void**)&h->zrec, sizeof(double) * nz));
     KFP_CUDA_TRY_H(cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream));
-    // elimination factors scaled for a right-hand side in units of m_off = hv/6:
-    // y_l = (g_l m_off) (M z)_l / m_off - (g_l a_l) y_{l-1} (periodic x: class 1 only)
-    const std::vector<double> coef = build_factors(g);
-    std::vector<double> tab((size_t)g.S * 2 * 2 * g.Lmax, 0.0);
-    const double m_off = g.hv / 6.0;
-    for (int s = 0; s < g.S; ++s)
-      for (int d = 0; d < 2; ++d) {
-        const double* gf = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 0) * g.Lmax];
-        const double* af = &coef[((((size_t)s * 3 + 1) * 2 + d) * 3 + 1) * g.Lmax];
-        double* t = &tab[(((size_t)s * 2 + d) * 2) * g.Lmax];
-        for (int l = 0; l < g.strips[s].L; ++l) {
-          t[l] = gf[l] * m_off;
-          t[g.Lmax + l] = gf[l] * af[l];
-        }
-      }
-    TRY(alloc(h, &h->fe_tab, tab.size() * es));
-    if (h->prec == KFP_F64) {
-      KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
-    } else {
-      const std::vector<float> t32(tab.begin(), tab.end());
-      KFP_CUDA_TRY_H(cudaMemcpy(h->fe_tab, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
-    }
+    TRY(alloc(h, &h->fe_tab, (size_t)g.S * 2 * 2 * g.Lmax * es));
+    TRY(upload_fe_tab(h, build_factors(g)));
   } else if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
     rc = setup_tma(h, pb);
     if (rc) return rc;
@@ -1272,8 +1280,8 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   return KFP_OK;
 }
 
-// New Robin parameters: strip table, LU factors, coefficient records and the
-// pre-scaled forcing are rebuilt in place (same sizes, so captured graphs stay valid).
+// New Robin parameters: strip table, LU factors, the split scheme's scaled
+// elimination factors, coefficient records and the pre-scaled forcing are rebuilt in place (same sizes, so captured graphs stay valid).
 template <typename T>
 kfp_status refresh_tables(kfp_swr* h) {
   Geometry& g = h->g;
@@ -1285,6 +1293,10 @@ kfp_status refresh_tables(kfp_swr* h) {
   } else {
     std::vector<float> c32(coef.begin(), coef.end());
     KFP_CUDA_TRY_H(cudaMemcpy(h->coef, c32.data(), sizeof(float) * c32.size(), cudaMemcpyHostToDevice));
+  }
+  if (g.split) {
+    kfp_status rc = upload_fe_tab(h, coef);
+    if (rc) return rc;
   }
   if (h->use_tma) {
     std::vector<T> rec, gf;

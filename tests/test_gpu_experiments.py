@@ -34,12 +34,13 @@ def test_classical_without_overlap_does_not_converge():
     assert not r["converged"] and r["true_error"] > 1e-2, r
 
 
-def test_p_scan_reuses_one_solver():
+@pytest.mark.parametrize("scheme", [0, 1], ids=["implicit_euler", "split_p1"])
+def test_p_scan_reuses_one_solver(scheme):
     from paper_1306_4596_gb300 import experiments as ex
     ps = [3.0, 4.23, 6.0]
-    scan = ex.p_scan(ps, j=0, overlap=3)
+    scan = ex.p_scan(ps, j=0, overlap=3, scheme=scheme)
     for p, row in zip(ps, scan):
-        fresh = ex.count_iterations(ex._problem(0, 3, True, p, None, parallel=False, seed=7))
+        fresh = ex.count_iterations(ex._problem(0, 3, True, p, None, parallel=False, seed=7, scheme=scheme))
         assert row["iters"] == fresh["iters"], (p, row, fresh["iters"])
         assert row["converged"]
 

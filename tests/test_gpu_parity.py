@@ -372,3 +372,30 @@ def test_split_scheme_converges_to_single_domain():
         s.sweep(300, tol=1e-13)
         u = s.solution()
     assert np.abs(u - mono).max() <= 1e-11 * np.abs(mono).max()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "mixed"])
+@pytest.mark.parametrize("overlap", [0, 2])
+def test_split_scheme_set_robin_equals_fresh_handle(overlap, precision):
+    """New Robin parameters on a live split-scheme handle reach both the elimination
+    (its pre-scaled factors) and the back-substitution: the results equal, bit for
+    bit, those of a handle created with the new parameters."""
+    swr = _swr()
+    prob = RD(89, 128, 5, 0.003, 4, overlap, True, p=4.0, seed=78, nforce=1).replace(
+        neumann_v=True, periodic_x=True, scheme=1)
+    newp, newq = np.array([2.0, 7.0, 3.0]), np.array([5.0, 1.5, 2.5])
+    with swr.SWR(prob, precision) as s:
+        s.sweep(2)
+        s.set_robin(newp, newq)
+        s.set_traces(prob.lam0)
+        s.sweep(3)
+        a = (s.solution(), s.traces())
+    fresh = prob.replace()
+    fresh.p, fresh.q = newp, newq
+    with swr.SWR(fresh, precision) as s:
+        s.sweep(3)
+        b = (s.solution(), s.traces())
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    if precision == "f64":
+        ref = run_oracle(fresh, 3)
+        assert rel_max(a[0], ref["u_T"]) <= F64_TOL and rel_max(a[1], ref["lam"]) <= F64_TOL
