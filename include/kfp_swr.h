@@ -145,9 +145,12 @@ kfp_status kfp_swr_create(const kfp_swr_desc* desc, const kfp_swr_problem* prob,
 kfp_status kfp_swr_sweep(kfp_swr_t h, int max_iters, double tol, int tol_kind, int* iters_done);
 
 /* Copy the current interface data lambda^k of interface `iface` (0..S-2), side 0
- * (lambda_1, data of the lower strip) or 1 (lambda_2, data of the upper strip):
- * [nt][nx+1] to dst (host, or device memory when dst_on_device).  Synchronises.
- * Errors: KFP_EINVAL, KFP_ECUDA. */
+ * (lambda_1 = Q_1 u of eq. "lambda12", the data that the lower strip takes at its
+ * top node beta_j) or 1 (lambda_2 = Q_2 u, the data that the upper strip takes at
+ * its bottom node alpha_j): [nt][nx+1], row n-1 at t^n, to dst (host, or device
+ * memory when dst_on_device; the caller owns dst).  After an iteration these are
+ * the data the next iteration uses (SWR2 and SWR4 of Section 6.3).  Synchronises.
+ * Errors: KFP_EINVAL (NULL handle or dst, iface or side out of range), KFP_ECUDA. */
 kfp_status kfp_swr_traces(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device);
 
 /* Replace the interface data by src [S-1][2][nt][nx+1] (host or device); used to
@@ -165,9 +168,14 @@ kfp_status kfp_swr_error(kfp_swr_t h, double* e_mis, double* e_chg, double* j_l2
  * strip) or 1 (upper strip): [nt][ov+1][nx+1], rows alpha_j..beta_j.  Synchronises. */
 kfp_status kfp_swr_bands(kfp_swr_t h, int iface, int side, double* dst, int dst_on_device);
 
-/* Copy the solution at t = T of the last iteration, [nv+1][nx+1]; node i comes from
- * the lower strip of interface j when i <= I_j and from the upper strip otherwise.
- * Synchronises.  Errors: KFP_EINVAL (no iteration has run), KFP_ECUDA. */
+/* Copy the solution at t = T of the last iteration, [nv+1][nx+1], to dst (host, or
+ * device memory when dst_on_device; the caller owns dst).  The paper defines the
+ * iterate only per subdomain (u_1^k on Omega_1, u_2^k on Omega_2, Section 6.3); on
+ * an overlap both strips hold a value, and this library takes node i from the lower
+ * strip of interface j when i <= I_j and from the upper strip otherwise (a tie-break
+ * of its own; the two values agree once the iteration has converged).
+ * Synchronises.  Errors: KFP_EINVAL (NULL handle or dst, no iteration has run),
+ * KFP_ECUDA. */
 kfp_status kfp_swr_solution(kfp_swr_t h, double* dst, int dst_on_device);
 
 /* Counters of this handle (all may be NULL): iterations run, cell-updates per
@@ -211,6 +219,9 @@ kfp_status kfp_swr_set_robin(kfp_swr_t h, const double* p, const double* q);
  *
  * bands: device memory, [nif][2][nt][overlap_cells+1][nx+1] FP64, the layout of
  *   kfp_swr_bands ([j][0] = lower strip, [j][1] = upper strip of interface j).
+ * periodic_x: nonzero for a problem created with KFP_FLAG_PERIODIC_X.  Column nx
+ *   then repeats column 0 and is left out of both sums, as kfp_swr_error does, so
+ *   that each node counts once; needs nx >= 2.
  * out:   device memory, 2 + 2*nif doubles, written by the kernel:
  *   out[0] = e_mis = max |lower - upper|, out[1] = j_l2 = dt hx sum (lower - upper)^2,
  *   out[2+2j], out[3+2j] = the same two norms of interface j alone.
@@ -224,12 +235,12 @@ kfp_status kfp_swr_set_robin(kfp_swr_t h, const double* p, const double* q);
  * the device), so make that first call before any stream capture.  Every call
  * shares the array: calls whose kernels can overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
- * Errors: KFP_EINVAL for NULL pointers, non-positive sizes or nif >
- * KFP_NOALLOC_MAX_INTERFACES; KFP_ECUDA if the set-up or the launch fails.
+ * Errors: KFP_EINVAL for NULL pointers, non-positive sizes, periodic_x with
+ * nx < 2 or nif > KFP_NOALLOC_MAX_INTERFACES; KFP_ECUDA if the set-up or the launch fails.
  * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
  */
-kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx, double dt,
-                                   double hx, double* out, void* cuda_stream);
+kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx,
+                                   int periodic_x, double dt, double hx, double* out, void* cuda_stream);
 
 /*
  * Check of the bounded device waits; the paper has no counterpart.  Every wait of
@@ -293,7 +304,10 @@ void kfp_batch_destroy(kfp_batch_t b);
 /* Message of the last error on b, or of the last failed kfp_batch_create (b = NULL). */
 const char* kfp_batch_last_error(kfp_batch_t b);
 
-/* Free every resource of the handle (NULL is ignored).  Synchronises its stream. */
+/* Free every resource of the handle: the device copies of the problem, the strip
+ * states, the interface data and overlap values, graphs and events.  This ends the
+ * iteration of Section 6.3; the paper has no further counterpart.  NULL is ignored;
+ * the handle must not be used afterwards.  Synchronises its stream; cannot fail. */
 void kfp_swr_destroy(kfp_swr_t h);
 
 /* Message of the last error on this handle ("" if none); valid until the next call. */

@@ -1,8 +1,9 @@
 // kfp_noalloc.cu -- interface norms computed without allocating any memory.
 //
 // kfp_iface_norms_noalloc reduces overlap values that the caller already holds in
-// device memory to the same norms as kfp_swr_error (e_mis and j_l2), plus the
-// same two norms per interface.  It is for callers that must not allocate: for
+// device memory to the same norms as kfp_swr_error (e_mis and j_l2; with periodic
+// x the repeated column nx is counted once, as there), plus the same two norms per
+// interface.  It is for callers that must not allocate: for
 // example a plugin that a host application hands only its input and output
 // buffers under a fixed device-memory budget, or a latency-critical loop that
 // cannot afford cudaMalloc, which may synchronise the device and takes the
@@ -80,20 +81,27 @@ kfp_status scratch_for_current_device(NoallocScratch** out) {
   return KFP_OK;
 }
 
-// grid (kBlocksPerIface, nif): block (b, j) reduces its share of interface j; the
-// last block to finish combines all partials in a fixed order and re-arms the ticket.
+// grid (kBlocksPerIface, nif): block (b, j) reduces its share of interface j -- the
+// rows (n, overlap node) b, b + kBlocksPerIface, ... of both sides, the first ncols
+// columns of each (ncols = nx with periodic x, whose column nx repeats column 0 and
+// is counted once, nx + 1 otherwise); the last block to finish combines all
+// partials in a fixed order and re-arms the ticket.
 __global__ void __launch_bounds__(kThreads)
-iface_norms_noalloc_kernel(const double* __restrict__ bands, int nif, size_t per_side, double dthx,
-                           NoallocScratch* scratch, double* __restrict__ out) {
+iface_norms_noalloc_kernel(const double* __restrict__ bands, int nif, size_t nrows, int nxp, int ncols,
+                           double dthx, NoallocScratch* scratch, double* __restrict__ out) {
   const int j = blockIdx.y;
+  const size_t per_side = nrows * (size_t)nxp;
   const double* lower = bands + ((size_t)j * 2 + 0) * per_side;
   const double* upper = bands + ((size_t)j * 2 + 1) * per_side;
   double mx = 0.0, sm = 0.0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_side;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const double d = lower[e] - upper[e];
-    mx = keep_nan_max(mx, fabs(d));
-    sm += d * d;
+  for (size_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const double* lo = lower + row * nxp;
+    const double* up = upper + row * nxp;
+    for (int m = threadIdx.x; m < ncols; m += blockDim.x) {
+      const double d = lo[m] - up[m];
+      mx = keep_nan_max(mx, fabs(d));
+      sm += d * d;
+    }
   }
   reduce_block(mx, sm);
   __shared__ bool is_last;
@@ -130,17 +138,19 @@ iface_norms_noalloc_kernel(const double* __restrict__ bands, int nif, size_t per
 }  // namespace
 
 extern "C" kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int overlap_cells, int nx,
-                                              double dt, double hx, double* out, void* cuda_stream) {
+                                              int periodic_x, double dt, double hx, double* out,
+                                              void* cuda_stream) {
   if (!bands || !out || nif < 1 || nt < 1 || overlap_cells < 0 || nx < 1 || !(dt > 0) || !(hx > 0))
     return KFP_EINVAL;
-  if (nif > kMaxIfaces) return KFP_EINVAL;  // more interfaces than the scratch array holds
+  if (periodic_x && nx < 2) return KFP_EINVAL;  // the periodic grid has at least two columns
+  if (nif > kMaxIfaces) return KFP_EINVAL;       // more interfaces than the scratch array holds
   NoallocScratch* scratch = nullptr;
   kfp_status rc = scratch_for_current_device(&scratch);
   if (rc) return rc;
-  const size_t per_side = (size_t)nt * (overlap_cells + 1) * (nx + 1);
+  const size_t nrows = (size_t)nt * (overlap_cells + 1);
   const dim3 grid(kBlocksPerIface, nif);
   iface_norms_noalloc_kernel<<<grid, kThreads, 0, (cudaStream_t)cuda_stream>>>(
-      bands, nif, per_side, dt * hx, scratch, out);
+      bands, nif, nrows, nx + 1, periodic_x ? nx : nx + 1, dt * hx, scratch, out);
   if (cudaGetLastError() != cudaSuccess) return KFP_ECUDA;
   return KFP_OK;
 }

@@ -113,7 +113,7 @@ def load(rebuild: bool = False):
             lib.kfp_swr_destroy.restype = None
             lib.kfp_swr_last_error.argtypes = [vp]
             lib.kfp_swr_last_error.restype = ctypes.c_char_p
-            lib.kfp_iface_norms_noalloc.argtypes = [vp, i, i, i, i, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.kfp_iface_norms_noalloc.argtypes = [vp, i, i, i, i, i, ctypes.c_double, ctypes.c_double, vp, vp]
             lib.kfp_iface_norms_noalloc.restype = ctypes.c_int
             lib.kfp_swr_create_error.argtypes = []
             lib.kfp_swr_create_error.restype = ctypes.c_char_p
@@ -213,14 +213,15 @@ def kfp_swr_destroy(h: int) -> None:
 
 
 def kfp_iface_norms_noalloc(bands_ptr: int, nif: int, nt: int, overlap_cells: int, nx: int, dt: float, hx: float,
-                            out_ptr: int, cuda_stream: int = 0) -> None:
+                            out_ptr: int, cuda_stream: int = 0, periodic_x: bool = False) -> None:
     """Interface norms from device-resident overlap values, with no allocation (see the header)."""
-    st = load().kfp_iface_norms_noalloc(bands_ptr, nif, nt, overlap_cells, nx, dt, hx, out_ptr, cuda_stream)
+    st = load().kfp_iface_norms_noalloc(bands_ptr, nif, nt, overlap_cells, nx, int(bool(periodic_x)), dt, hx,
+                                        out_ptr, cuda_stream)
     if st != KFP_OK:
         if st == KFP_EINVAL and nif > KFP_NOALLOC_MAX_INTERFACES:
             msg = f"nif = {nif} exceeds KFP_NOALLOC_MAX_INTERFACES = {KFP_NOALLOC_MAX_INTERFACES}"
         elif st == KFP_EINVAL:
-            msg = "NULL pointer or non-positive size"
+            msg = "NULL pointer, non-positive size, or periodic x with nx < 2"
         else:
             msg = "device set-up or kernel launch failed"
         raise KfpError(st, f"kfp_iface_norms_noalloc: {msg}")

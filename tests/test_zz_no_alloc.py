@@ -38,12 +38,17 @@ def _bands_and_norms(prob, iters):
 @pytest.mark.parametrize("factory", [
     lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=11),
     lambda: inputs.gaussian_bumps(130, 256, 30, 1.5e-3, 4, seed=12, overlap=4, robin=False),
-], ids=["robin_8_strips", "dirichlet_overlap_4"])
+    # periodic x (the model problem): column nx repeats column 0 and counts once
+    lambda: inputs.gaussian_bumps(119, 256, 30, 1.5e-3, 4, p=4.0, seed=13, overlap=2).replace(
+        periodic_x=True, neumann_v=True),
+], ids=["robin_8_strips", "dirichlet_overlap_4", "periodic_x_overlap_2"])
 def test_noalloc_norms_match_kfp_swr_error(factory):
     import torch
     from paper_1306_4596_gb300 import swr
 
     prob = factory()
+    periodic = bool(prob.periodic_x)
+    ncols = prob.nx if periodic else prob.nx + 1
     nif = prob.nstrips - 1
     bands, e_mis, j_l2 = _bands_and_norms(prob, 2)
     out = torch.empty(2 + 2 * nif, dtype=torch.float64, device="cuda")
@@ -51,7 +56,7 @@ def test_noalloc_norms_match_kfp_swr_error(factory):
     for _ in range(2):  # the scratch array is reused from one call to the next
         out.fill_(float("nan"))
         swr.kfp_iface_norms_noalloc(bands.data_ptr(), nif, prob.nt, prob.overlap, prob.nx, prob.dt, prob.hx,
-                                    out.data_ptr(), stream)
+                                    out.data_ptr(), stream, periodic_x=periodic)
         torch.cuda.synchronize()
         o = out.cpu().numpy()
         assert np.isfinite(o).all()
@@ -61,7 +66,7 @@ def test_noalloc_norms_match_kfp_swr_error(factory):
         assert per[:, 0].max() == o[0]
         assert abs(per[:, 1].sum() - o[1]) <= TOL * o[1]
         b = bands.cpu().numpy()
-        d = b[:, 0] - b[:, 1]
+        d = (b[:, 0] - b[:, 1])[..., :ncols]
         np.testing.assert_allclose(per[:, 0], np.abs(d).reshape(nif, -1).max(axis=1), rtol=0, atol=0)
         np.testing.assert_allclose(per[:, 1], prob.dt * prob.hx * (d * d).reshape(nif, -1).sum(axis=1),
                                    rtol=TOL)
@@ -76,5 +81,8 @@ def test_noalloc_rejects_more_interfaces_than_its_scratch():
     out = torch.zeros(2 + 2 * nif, dtype=torch.float64, device="cuda")
     with pytest.raises(swr.KfpError) as ei:
         swr.kfp_iface_norms_noalloc(bands.data_ptr(), nif, 1, 0, 1, 0.1, 0.5, out.data_ptr(), 0)
+    assert ei.value.status == swr.KFP_EINVAL
+    with pytest.raises(swr.KfpError) as ei:  # a periodic grid needs two columns
+        swr.kfp_iface_norms_noalloc(bands.data_ptr(), 1, 1, 0, 1, 0.1, 0.5, out.data_ptr(), 0, periodic_x=True)
     assert ei.value.status == swr.KFP_EINVAL
     assert math.isclose(out.abs().sum().item(), 0.0)
