@@ -82,6 +82,11 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
                                   * node 0 in every output; bc_xin, column nx of u0 and f_space, and
                                   * column nx of lambda0 / set_traces data are ignored (replaced by
                                   * column 0); needs nx >= 2 */
+#define KFP_FLAG_PERSISTENT 128u /* run the nt-1 interior sweep passes of an iteration in one co-resident
+                                  * (cooperative) launch, each unit (strip, block of 120 columns) waiting
+                                  * on its column neighbours' completion counters, instead of one launch
+                                  * per pass; the TMA-fed sweep without periodic x only (ignored
+                                  * otherwise).  Results are bitwise those of the per-pass form */
 #define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each
                                   * step (M + dt S) w = M (u^n + dt f^{n+1}) with P1 elements in v
                                   * (mass M, stiffness S; Robin ends add dt p or dt q to the end row
@@ -253,6 +258,40 @@ kfp_status kfp_iface_norms_noalloc(const double* bands, int nif, int nt, int ove
  * KFP_ENOMEM, KFP_ECUDA.
  */
 kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream);
+
+/*
+ * Check of the bounded waits between the units of the persistent sweep; the paper
+ * has no counterpart.  The persistent sweep (KFP_FLAG_PERSISTENT) runs the interior
+ * passes of an iteration in one launch, and before a unit (strip, block of 120
+ * columns) starts pass k it waits until its column neighbours have finished pass k-1.  This
+ * runs the sweep passes of one iteration once with unit `unit` never reporting
+ * completion, so that its neighbours' waits give up after `limit_s` seconds, raise
+ * the error flag and every block leaves; the interface data, history and counters
+ * of the handle are not touched, the flag is cleared afterwards, and the next
+ * kfp_swr_sweep runs as if this call had not happened.  Synchronises.
+ * Returns KFP_ETIMEOUT when the waits gave up as designed (KFP_OK would mean the
+ * stalled unit went unnoticed); KFP_ENOTSUP when the handle does not use the
+ * persistent sweep; KFP_EINVAL for a unit outside 0..units-1 or limit_s outside
+ * (0, 10] or nt < 3 (fewer than two interior passes); KFP_ECUDA.
+ */
+kfp_status kfp_swr_selftest_stall(kfp_swr_t h, int unit, double limit_s);
+
+/*
+ * FP64 fused multiply-add rate of the current device, for the roofline of the FP64
+ * sweep (which the FP64 pipe, not HBM, bounds); the paper has no counterpart.  One
+ * block of 32 * warps_per_sm threads per SM, each thread running `chains` (1, 2, 4
+ * or 8) independent recurrences x <- x a + b for 8 * steps dependent steps, timed
+ * with CUDA events on cuda_stream after a short warm-up launch.  *dfma_per_s
+ * receives the lane-level DFMA operations per second (2 flops each); *sm_mhz (may
+ * be NULL) the SM clock seen during the run (cycle counter over nanosecond timer of
+ * block 0).  Many warps with several chains give the pipe's throughput; one warp per
+ * sub-partition with one chain gives 1 / (dependent DFMA latency).  Allocates and
+ * frees its own small buffers; synchronises.  Errors: KFP_EINVAL (chains not in
+ * {1,2,4,8}, warps_per_sm outside 1..32, steps < 1, NULL dfma_per_s), KFP_ENOMEM,
+ * KFP_ECUDA.
+ */
+kfp_status kfp_probe_fp64_rate(int chains, int warps_per_sm, int steps, double* dfma_per_s, double* sm_mhz,
+                               void* cuda_stream);
 
 /* Iteration counters (any pointer may be NULL): iterations whose strip solves ran
  * in FP64 and in FP32 (for KFP_MIXED: outer FP64 steps and inner FP32 correction

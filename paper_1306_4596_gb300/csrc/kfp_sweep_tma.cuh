@@ -111,6 +111,7 @@ struct TmaSmem {
   T rec[NST][kChunk][kRecW];
   uint64_t full[NST];
   uint64_t empty[NST];
+  int abort;  // set by the producer before it completes a stage without data
 };
 
 // Fields 0..3 of a record (ncp, A, B, -g a) as vector loads.
@@ -205,6 +206,7 @@ __device__ __forceinline__ void init_ring(TmaSmem<T, NST>& sm) {
       mbar_init(&sm.full[q], 1);
       mbar_init(&sm.empty[q], kWarpsPerBlock);
     }
+    sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -335,6 +337,7 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
       atomicExch(X.flag, 1);
       return false;
     }
+    if (*(volatile int*)&sm.abort) return false;  // the producer gave up (stage holds no data)
     const int l0 = chunk_l0(c);
     const int l1 = l0 + kChunk - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
@@ -508,6 +511,131 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
   TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
   init_ring(sm);
   (void)pass_unit<T, UP, MODE, FMODE, NST>(maps, X, k, blockIdx.y + X.p.strip0, blockIdx.x, sm, 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: the nt-1 interior passes of an iteration in one launch.
+// ---------------------------------------------------------------------------
+//
+// The first pass (elimination of step 1 from u^0) and the last (back-substitution
+// of step nt) stay launches of their own: inlining those two variants as well made
+// the FP64 kernel spill.
+//
+// The work of a pass is a list of units (strip s, column block bx); unit u = s * nbx
+// + bx.  Every block of a co-resident grid (cooperative launch) owns the units
+// blockIdx.x, blockIdx.x + gridDim.x, ... and walks them pass by pass, keeping its
+// TMA ring running across units and passes.  Pass k of unit u reads the residue
+// y^k of its own columns and of one halo column on each side, which the units u-1
+// and u+1 of the same strip wrote in pass k-1, and it overwrites the buffer those
+// units read in pass k-1.  So before the producer loads pass k of u it waits until
+// units u-1, u and u+1 have completed pass k-1; completion is a per-unit counter to
+// which every consumer warp adds one after its stores of a pass (no barrier inside
+// the block, so a warp that leaves on an error cannot strand the others).  Neighbours are then never more
+// than one pass apart, which is what the two residue buffers allow.  With one unit
+// per block the wait exposes one counter round trip per pass; with several, the
+// neighbours finished long before and the ring streams on.
+//
+// Every counter wait is bounded by wall time (globaltimer); on expiry, or when
+// another block has raised the error flag, the producer marks the ring aborted and
+// completes the next stage without data, so its consumers leave as well.
+
+struct PersistArgs {
+  unsigned* done;                 // [nunits] consumer warps x passes completed in this launch
+                                  // (zeroed before it)
+  int k_begin, k_end;             // passes k_begin .. k_end-1 (interior passes: 1 <= k < nt)
+  int nunits, nbx;                // units of the launch, column blocks per strip
+  int stall_unit;                 // self-test: this unit never reports completion (-1: none)
+  unsigned long long wait_ns;     // limit of one counter wait
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Order this thread's generic-proxy global accesses with later async-proxy (TMA)
+// accesses, and the other way round.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Bounded wait until done[a], done[b], done[c] (b, c may be -1) all reach target.
+// False on time-out (the error flag is raised) or when the error flag is already set.
+__device__ __forceinline__ bool wait_done(const PersistArgs& P, const int* err, int a, int b, int c,
+                                          unsigned target) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    bool ok = ld_acquire_u32(P.done + a) >= target;
+    if (b >= 0) ok = ok && ld_acquire_u32(P.done + b) >= target;
+    if (c >= 0) ok = ok && ld_acquire_u32(P.done + c) >= target;
+    if (ok) return true;
+    if ((it & 15) == 15) {
+      if (*(volatile const int*)err) return false;
+      if (global_ns() - t0 > P.wait_ns) {
+        atomicExch(const_cast<int*>(err), 1);
+        return false;
+      }
+    }
+  }
+}
+
+// Interior pass k (back-substitution of step k, elimination of step k+1) of one
+// unit; pass k runs upward when k is even.
+template <typename T, int FMODE, int NST>
+__device__ __forceinline__ bool pass_unit_k(const TmaMaps& maps, const TmaArgs<T>& X, int k, int s, int bx,
+                                            TmaSmem<T, NST>& sm, unsigned cbase) {
+  return (k & 1) ? pass_unit<T, false, 1, FMODE, NST>(maps, X, k, s, bx, sm, cbase)
+                 : pass_unit<T, true, 1, FMODE, NST>(maps, X, k, s, bx, sm, cbase);
+}
+
+template <typename T, int FMODE, int NST>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+sweep_persistent_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const PersistArgs P) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  init_ring(sm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool producer = warp == kWarpsPerBlock;
+  unsigned cbase = 0;
+  for (int k = P.k_begin; k < P.k_end; ++k) {
+    for (int u = blockIdx.x; u < P.nunits; u += gridDim.x) {
+      const int sl = u / P.nbx, bx = u - sl * P.nbx;
+      const int s = sl + X.p.strip0;
+      const int nc = (X.p.strips[s].L + kChunk - 1) / kChunk;
+      if (producer && lane == 0 && k > P.k_begin) {
+        const bool ok = wait_done(P, X.flag, u, bx > 0 ? u - 1 : -1, bx + 1 < P.nbx ? u + 1 : -1,
+                                  (unsigned)((k - P.k_begin) * kWarpsPerBlock));
+        if (!ok) {
+          // complete the next stage without data: the consumers see the abort word
+          sm.abort = 1;
+          const int q = (int)(cbase % NST);
+          const unsigned use = cbase / NST;
+          if (use == 0 || mbar_wait(&sm.empty[q], (use - 1) & 1)) mbar_arrive(&sm.full[q]);
+          return;
+        }
+        fence_proxy_async_global();
+      }
+      const bool ok = pass_unit_k<T, FMODE, NST>(maps, X, k, s, bx, sm, cbase);
+      if (!ok) return;
+      if (!producer) {
+        // this warp's stores of pass k are visible (to loads and to TMA) before the
+        // unit's counter moves; each consumer warp adds one
+        __threadfence();
+        fence_proxy_async_global();
+        __syncwarp();
+        if (lane == 0 && u != P.stall_unit) red_release_add_u32(P.done + u, 1u);
+      }
+      cbase += (unsigned)nc;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -250,6 +250,11 @@ struct kfp_swr {
   void* rec = nullptr;         // [S][2][Lpad][24] coefficient records
   int* flag = nullptr;         // device error flag (bounded waits)
   int use_tma = 0, fmode = 0, Lpad = 0;
+  // persistent sweep: one co-resident launch per iteration (per strip in the serial form)
+  int persist = 0, persist_grid = 0, nbx = 0;
+  unsigned* done = nullptr;    // [S * nbx] per-unit completion counters
+  int stall_unit = -1;         // self-test only
+  unsigned long long wait_ns = 4000000000ull;
   kfp::TmaMaps maps;
   void* UT = nullptr;
   void* U0 = nullptr;
@@ -319,6 +324,7 @@ struct kfp_swr {
   size_t elem() const { return prec == KFP_F64 ? sizeof(double) : sizeof(float); }
   int launches_per_iter() const {
     const int groups = (flags & KFP_FLAG_GAUSS_SEIDEL) ? g.S : 1;
+    if (persist) return groups * (g.nt > 1 ? 3 : 2) + 2;
     return (g.nt + 1 + (g.periodic ? g.nt : 0)) * groups + 2;
   }
 
@@ -428,8 +434,60 @@ struct kfp_swr {
   template <typename T>
   static size_t tma_smem_bytes() { return sizeof(kfp::TmaSmem<T, tma_stages<T>()>) + 128; }
 
+  // The persistent sweep, per group of strips (all strips; one strip at a time in the
+  // serial form): the first pass, the nt-1 interior passes in one cooperative launch
+  // (after the units' completion counters are zeroed), the last pass.
+  template <typename T, int FM>
+  void enqueue_persistent(cudaStream_t st, bool interior_only = false) const {
+    constexpr int NST = tma_stages<T>();
+    kfp::TmaArgs<T> X = tma_args<T>();
+    const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+    const int groups = serial ? g.S : 1;
+    const dim3 pgrid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
+    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
+    const size_t smem = tma_smem_bytes<T>();
+    if (g.nt > 1) cudaMemsetAsync(done, 0, sizeof(unsigned) * (size_t)g.S * nbx, st);
+    for (int grp = 0; grp < groups; ++grp) {
+      X.p.strip0 = serial ? grp : 0;
+      if (!interior_only) kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<pgrid, block, smem, st>>>(maps, X, 0);
+      if (g.nt > 1) enqueue_interior<T, FM>(st, X, serial);
+      if (interior_only) continue;
+      if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
+      else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
+    }
+  }
+
+  template <typename T, int FM>
+  void enqueue_interior(cudaStream_t st, const kfp::TmaArgs<T>& X, bool serial) const {
+    constexpr int NST = tma_stages<T>();
+    kfp::PersistArgs P;
+    P.k_begin = 1;
+    P.k_end = g.nt;
+    P.nbx = nbx;
+    P.nunits = (serial ? 1 : g.S) * nbx;
+    P.done = done + (size_t)X.p.strip0 * nbx;
+    P.stall_unit = stall_unit;
+    P.wait_ns = wait_ns;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min(persist_grid, P.nunits));
+    cfg.blockDim = dim3((kfp::kWarpsPerBlock + 1) * 32);
+    cfg.dynamicSmemBytes = tma_smem_bytes<T>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kfp::sweep_persistent_kernel<T, FM, NST>, maps, X, P);
+  }
+
+
   template <typename T, int FM>
   void enqueue_passes_tma(cudaStream_t st) const {
+    if (persist) {
+      enqueue_persistent<T, FM>(st);
+      return;
+    }
     constexpr int NST = tma_stages<T>();
     kfp::TmaArgs<T> X = tma_args<T>();
     const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
@@ -464,7 +522,23 @@ struct kfp_swr {
     set((const void*)kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST>);
     set((const void*)kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST>);
     set((const void*)kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST>);
+    set((const void*)kfp::sweep_persistent_kernel<T, FM, NST>);
     return e;
+  }
+
+  // Blocks of the persistent sweep that fit on the device at once (0 if none).
+  template <typename T, int FM>
+  int persistent_capacity() const {
+    constexpr int NST = tma_stages<T>();
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_persistent_kernel<T, FM, NST>,
+                                                      (kfp::kWarpsPerBlock + 1) * 32, tma_smem_bytes<T>()) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per_sm * sms;
   }
 
   void record(int idx, cudaStream_t st, bool capturing) const {
@@ -739,7 +813,7 @@ struct kfp_swr {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    void* bufs[] = {Ybuf, GF, rec, flag, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
+    void* bufs[] = {Ybuf, GF, rec, flag, done, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, zrec, fe_tab, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
     for (void* b : bufs)
@@ -961,6 +1035,21 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
                                 : (h->fmode == 1 ? h->set_tma_smem_attr<T, 1>() : h->set_tma_smem_attr<T, 2>());
   if (e != cudaSuccess) return h->fail(KFP_ECUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
   h->use_tma = 1;
+  // Persistent sweep on request; periodic x needs its column wrap between passes and
+  // keeps one launch per pass.
+  if ((h->flags & KFP_FLAG_PERSISTENT) && !g.periodic) {
+    KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
+    const int cap = h->fmode == 0 ? h->persistent_capacity<T, 0>()
+                                  : (h->fmode == 1 ? h->persistent_capacity<T, 1>() : h->persistent_capacity<T, 2>());
+    if (cap >= 1) {
+      h->nbx = (g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock;
+      rc = alloc(h, (void**)&h->done, sizeof(unsigned) * (size_t)g.S * h->nbx);
+      if (rc) return rc;
+      KFP_CUDA_TRY_H(cudaMemset(h->done, 0, sizeof(unsigned) * (size_t)g.S * h->nbx));
+      h->persist_grid = cap;
+      h->persist = 1;
+    }
+  }
   return KFP_OK;
 }
 
@@ -1873,6 +1962,38 @@ __global__ void bounded_wait_selftest_kernel(int* flag, unsigned limit) {
 }
 
 }  // namespace
+
+extern "C" kfp_status kfp_swr_selftest_stall(kfp_swr_t h, int unit, double limit_s) {
+  if (!h) return KFP_EINVAL;
+  if (!h->persist) return h->fail(KFP_ENOTSUP, "the handle does not use the persistent sweep");
+  const int units = ((h->flags & KFP_FLAG_GAUSS_SEIDEL) ? 1 : h->g.S) * h->nbx;
+  if (unit < 0 || unit >= units) return h->fail(KFP_EINVAL, "unit %d outside 0..%d", unit, units - 1);
+  if (!(limit_s > 0) || limit_s > 10) return h->fail(KFP_EINVAL, "limit_s must be in (0, 10]");
+  if (h->g.nt < 3) return h->fail(KFP_EINVAL, "the check needs nt >= 3 (two interior passes)");
+  KFP_CUDA_TRY_ON(h, cudaStreamSynchronize(h->stream));
+  const unsigned long long keep = h->wait_ns;
+  h->stall_unit = unit;
+  h->wait_ns = (unsigned long long)(limit_s * 1e9);
+  // the interior sweep passes only: the interface data and the norms stay as they are
+  if (h->prec == KFP_F64) {
+    if (h->fmode == 0) h->enqueue_persistent<double, 0>(h->stream, true);
+    else if (h->fmode == 1) h->enqueue_persistent<double, 1>(h->stream, true);
+    else h->enqueue_persistent<double, 2>(h->stream, true);
+  } else {
+    if (h->fmode == 0) h->enqueue_persistent<float, 0>(h->stream, true);
+    else if (h->fmode == 1) h->enqueue_persistent<float, 1>(h->stream, true);
+    else h->enqueue_persistent<float, 2>(h->stream, true);
+  }
+  h->stall_unit = -1;
+  h->wait_ns = keep;
+  KFP_CUDA_TRY_ON(h, cudaGetLastError());
+  KFP_CUDA_TRY_ON(h, cudaStreamSynchronize(h->stream));
+  int f = 0;
+  KFP_CUDA_TRY_ON(h, cudaMemcpy(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
+  KFP_CUDA_TRY_ON(h, cudaMemset(h->flag, 0, sizeof(int)));
+  KFP_CUDA_TRY_ON(h, cudaDeviceSynchronize());
+  return f ? KFP_ETIMEOUT : KFP_OK;
+}
 
 extern "C" kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream) {
   if (limit == 0) return KFP_EINVAL;

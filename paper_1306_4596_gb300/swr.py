@@ -24,7 +24,7 @@ KFP_DIRICHLET, KFP_ROBIN = 0, 1
 KFP_F64, KFP_F32, KFP_MIXED = 0, 1, 2
 PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
 KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1, 2, 4, 8
-KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME = 16, 32, 64
+KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME, KFP_FLAG_PERSISTENT = 16, 32, 64, 128
 
 
 def problem_flags(prob) -> int:
@@ -39,7 +39,7 @@ EXPORTED = ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_tr
             "kfp_swr_last_error", "kfp_swr_create_error", "kfp_iface_norms_noalloc", "kfp_swr_counters",
             "kfp_batch_create", "kfp_batch_configure", "kfp_batch_sweep", "kfp_batch_instance", "kfp_batch_stats",
             "kfp_batch_destroy", "kfp_batch_last_error", "kfp_swr_gradient", "kfp_swr_set_robin",
-            "kfp_selftest_bounded_wait")
+            "kfp_selftest_bounded_wait", "kfp_swr_selftest_stall", "kfp_probe_fp64_rate")
 KFP_NOALLOC_MAX_INTERFACES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -115,6 +115,10 @@ def load(rebuild: bool = False):
             lib.kfp_swr_last_error.restype = ctypes.c_char_p
             lib.kfp_iface_norms_noalloc.argtypes = [vp, i, i, i, i, i, ctypes.c_double, ctypes.c_double, vp, vp]
             lib.kfp_iface_norms_noalloc.restype = ctypes.c_int
+            lib.kfp_probe_fp64_rate.argtypes = [i, i, i, _dp, _dp, vp]
+            lib.kfp_probe_fp64_rate.restype = ctypes.c_int
+            lib.kfp_swr_selftest_stall.argtypes = [vp, i, ctypes.c_double]
+            lib.kfp_swr_selftest_stall.restype = ctypes.c_int
             lib.kfp_swr_create_error.argtypes = []
             lib.kfp_swr_create_error.restype = ctypes.c_char_p
             for name in ("kfp_swr_create", "kfp_swr_sweep", "kfp_swr_traces", "kfp_swr_set_traces",
@@ -233,6 +237,21 @@ def kfp_selftest_bounded_wait(limit: int = 1 << 16, cuda_stream: int = 0) -> int
     lib = load()
     lib.kfp_selftest_bounded_wait.argtypes = [ctypes.c_uint, ctypes.c_void_p]
     return int(lib.kfp_selftest_bounded_wait(limit, cuda_stream))
+
+
+def kfp_swr_selftest_stall(h: int, unit: int, limit_s: float) -> int:
+    """Run the sweep passes once with one unit never reporting completion (see the
+    header); returns the status, KFP_ETIMEOUT when the waits gave up as designed."""
+    return int(load().kfp_swr_selftest_stall(h, unit, limit_s))
+
+
+def kfp_probe_fp64_rate(chains: int = 8, warps_per_sm: int = 16, steps: int = 20000, cuda_stream: int = 0):
+    """(DFMA operations per second, SM MHz during the run) of the current device (see the header)."""
+    rate, mhz = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().kfp_probe_fp64_rate(chains, warps_per_sm, steps, ctypes.byref(rate), ctypes.byref(mhz), cuda_stream)
+    if st != KFP_OK:
+        raise KfpError(st, "kfp_probe_fp64_rate failed")
+    return rate.value, mhz.value
 
 
 def kfp_swr_last_error(h: int) -> str:
@@ -369,7 +388,7 @@ class SWR:
     handed over and the library copies them in."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
-                 graph: bool = True, profile: bool = False, generic: bool = False):
+                 graph: bool = True, profile: bool = False, generic: bool = False, persistent: bool = False):
         import torch
 
         self.prob = prob
@@ -395,7 +414,7 @@ class SWR:
         self._p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
         self._q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
         flags = ((0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
-                 | (KFP_FLAG_GENERIC if generic else 0)
+                 | (KFP_FLAG_GENERIC if generic else 0) | (KFP_FLAG_PERSISTENT if persistent else 0)
                  | problem_flags(prob))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
