@@ -1,10 +1,11 @@
 """Build the sm_103a shared library ``_build/libkfp_swr.so`` with nvcc.
 
-Two translation units (``csrc/kfp_swr.cu``, which includes the kernels, and
-``csrc/kfp_noalloc.cu``), one
-``-gencode`` (compute_103a / sm_103a), built in-tree so that the process loading
-it is seen using it.  Host code is compiled without floating-point contraction so
-that its setup arithmetic (grid nodes, factors) rounds the same on x86 and Arm.
+Translation units (``csrc/kfp_swr.cu``, which includes the kernels,
+``csrc/kfp_noalloc.cu`` and ``csrc/kfp_probe.cu``) are compiled to objects in
+parallel, one ``-gencode`` (compute_103a / sm_103a), then linked; built in-tree
+so that the process loading it is seen using it.  Host code is compiled without
+floating-point contraction so that its setup arithmetic (grid nodes, factors)
+rounds the same on x86 and Arm.
 """
 from __future__ import annotations
 
@@ -17,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkfp_swr.so")
-SOURCES = [os.path.join(CSRC, "kfp_swr.cu"), os.path.join(CSRC, "kfp_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, "kfp_swr.cu"), os.path.join(CSRC, "kfp_noalloc.cu"), os.path.join(CSRC, "kfp_probe.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, "kfp_swr.h")]
 
@@ -25,7 +26,6 @@ NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC,-ffp-contract=off",
-    "-shared",
 ]
 
 
@@ -48,14 +48,32 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({' '.join(cmd)}):\n{res.stdout}\n{res.stderr}")
-    if verbose:
-        print(res.stdout, res.stderr)
+    tag = f".tmp{os.getpid()}"
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", tag + ".o"))
+        cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-c", "-o", obj, src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    failed = []
+    for cmd, proc in procs:
+        out, err = proc.communicate()
+        if proc.returncode != 0:
+            failed.append(f"nvcc failed ({' '.join(cmd)}):\n{out}\n{err}")
+        elif verbose:
+            print(out, err)
+    tmp = LIB + tag + ".so"
+    if not failed:
+        cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            failed.append(f"link failed ({' '.join(cmd)}):\n{res.stdout}\n{res.stderr}")
+    for obj in objs:
+        if os.path.exists(obj):
+            os.remove(obj)
+    if failed:
+        raise RuntimeError("\n".join(failed))
     os.replace(tmp, LIB)
     return LIB
