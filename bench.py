@@ -252,7 +252,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=20, help="Adam steps of the adjoint leg (0 = skip it)")
     ap.add_argument("--ref-nt", type=int, default=6, help="time steps per reference-arm step")
     ap.add_argument("--persistent", action="store_true",
-                    help="the persistent sweep (interior passes in one launch) instead of one launch per pass")
+                    help="always the streamed sweep (interior passes in one launch)")
+    ap.add_argument("--per-pass", action="store_true", help="always one launch per pass")
     ap.add_argument("--nt", type=int, default=None,
                     help="shorter time window (profiling captures only; the JSON line records it)")
     args = ap.parse_args()
@@ -286,7 +287,8 @@ def main():
     cells_per_iter = swr_mod.cell_updates_per_iteration(prob)
 
     # ---- headline: device-resident inputs, profiled sweep ------------------------
-    solver = swr_mod.SWR(prob, args.precision, inputs_on="device", profile=True, persistent=args.persistent)
+    solver = swr_mod.SWR(prob, args.precision, inputs_on="device", profile=True,
+                         persistent=True if args.persistent else (False if args.per_pass else None))
     ms, clocks = time_iterations(torch, solver, args.steps, args.warmup, dist, world, device_index)
     st = solver.stats()
     iters_total = st["iterations"]

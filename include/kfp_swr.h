@@ -82,11 +82,13 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
                                   * node 0 in every output; bc_xin, column nx of u0 and f_space, and
                                   * column nx of lambda0 / set_traces data are ignored (replaced by
                                   * column 0); needs nx >= 2 */
-#define KFP_FLAG_PERSISTENT 128u /* run the nt-1 interior sweep passes of an iteration in one co-resident
-                                  * (cooperative) launch, each unit (strip, block of 120 columns) waiting
-                                  * on its column neighbours' completion counters, instead of one launch
-                                  * per pass; the TMA-fed sweep without periodic x only (ignored
-                                  * otherwise).  Results are bitwise those of the per-pass form */
+/* How the nt-1 interior sweep passes of an iteration are launched (TMA-fed sweep
+ * without periodic x; results are bitwise the same either way).  By default the
+ * library runs them in one co-resident (cooperative) launch -- the streamed sweep --
+ * when a pass has more units (strip x block of 120 columns) than the GPU holds
+ * blocks at once, and one launch per pass otherwise (measured faster there). */
+#define KFP_FLAG_PERSISTENT 128u /* always the streamed sweep */
+#define KFP_FLAG_PER_PASS 256u   /* always one launch per pass */
 #define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each
                                   * step (M + dt S) w = M (u^n + dt f^{n+1}) with P1 elements in v
                                   * (mass M, stiffness S; Robin ends add dt p or dt q to the end row
@@ -261,7 +263,7 @@ kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream);
 
 /*
  * Check of the bounded waits between the units of the persistent sweep; the paper
- * has no counterpart.  The persistent sweep (KFP_FLAG_PERSISTENT) runs the interior
+ * has no counterpart.  The streamed sweep (see KFP_FLAG_PERSISTENT) runs the interior
  * passes of an iteration in one launch, and before a unit (strip, block of 120
  * columns) starts pass k it waits until its column neighbours have finished pass k-1.  This
  * runs the sweep passes of one iteration once with unit `unit` never reporting
@@ -271,7 +273,7 @@ kfp_status kfp_selftest_bounded_wait(unsigned limit, void* cuda_stream);
  * kfp_swr_sweep runs as if this call had not happened.  Synchronises.
  * Returns KFP_ETIMEOUT when the waits gave up as designed (KFP_OK would mean the
  * stalled unit went unnoticed); KFP_ENOTSUP when the handle does not use the
- * persistent sweep; KFP_EINVAL for a unit outside 0..units-1 or limit_s outside
+ * streamed sweep; KFP_EINVAL for a unit outside 0..units-1 or limit_s outside
  * (0, 10] or nt < 3 (fewer than two interior passes); KFP_ECUDA.
  */
 kfp_status kfp_swr_selftest_stall(kfp_swr_t h, int unit, double limit_s);

@@ -104,6 +104,27 @@ struct TmaArgs {
   int bc_data;         // caller gave x-inflow or v-boundary data (rows of kind 1/2 need it)
 };
 
+// Work description the producer of the streamed sweep writes into the stage of a
+// unit's first chunk (k < 0: no more work).  The pass arguments travel with it: read
+// from shared memory they cannot alias the consumers' global stores, so the
+// compiler need not reload them after each store (as it must from global memory).
+struct StreamTail {
+  StripInfo st;                // the unit's strip
+  int k, inst, strip, bx, nc, unit, new_args;
+};
+template <typename T>
+struct StreamHeader {
+  TmaArgs<T> args;             // the unit's problem (written only when it changes: new_args)
+  StreamTail tail;
+};
+
+// Copy n 32-bit words from src to dst, lane `lane` of `lanes` copying every lanes-th.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int n, int lane, int lanes) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = lane; i < n; i += lanes) d[i] = s[i];
+}
+
 template <typename T, int NST>
 struct TmaSmem {
   T tile[NST][kChunk][kBoxW];
@@ -111,6 +132,10 @@ struct TmaSmem {
   T rec[NST][kChunk][kRecW];
   uint64_t full[NST];
   uint64_t empty[NST];
+  StreamHeader<T> hdr[NST];
+  // each consumer warp's copy of the header of the unit it is running: once the
+  // unit's first stage is released, a later unit's header may land in that stage
+  StreamHeader<T> cur[kWarpsPerBlock];
   int abort;  // set by the producer before it completes a stage without data
 };
 
@@ -212,58 +237,68 @@ __device__ __forceinline__ void init_ring(TmaSmem<T, NST>& sm) {
   __syncthreads();
 }
 
-// One work unit: strip s, column block bx (4 warps = 120 output columns) of one
-// problem, for pass k.  Ring slots continue from chunk number cbase (so a block can
-// run several units back to back).  Returns false if a bounded wait expired.
+// Producer half of one unit's pass (one elected lane): issue the TMA loads of its
+// NC chunks into the ring, from chunk number cbase on; with TAIL, write the unit's
+// header (and, when tail->new_args, a copy of X) into the stage of the first chunk
+// before that stage is released.  Returns false if a
+// bounded wait expired (the copies already issued are drained first).
 template <typename T, bool UP, int MODE, int FMODE, int NST>
-__device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
-                                          const int bx, TmaSmem<T, NST>& sm, const unsigned cbase) {
-  const PassArgs<T>& A = X.p;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const StripInfo st = A.strips[s];
+__device__ __forceinline__ bool produce_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
+                                             const int bx, const StripInfo& st, TmaSmem<T, NST>& sm,
+                                             const unsigned cbase, const StreamTail* tail) {
   const int L = st.L;
   const int NC = (L + kChunk - 1) / kChunk;
   constexpr bool kUseForce = (MODE != 2) && (FMODE != 0);
   const int dir = UP ? 0 : 1;
-
-  auto chunk_l0 = [&](int c) { return UP ? c * kChunk : L - (c + 1) * kChunk; };
-
-  if (warp == kWarpsPerBlock) {
-    // ------------------------------ producer ------------------------------
-    if (lane == 0) {
-      const int x0 = bx * (kWarpsPerBlock * kOutCols);
-      const unsigned bytes = (unsigned)(sizeof(T) * (kChunk * kBoxW * (kUseForce ? 2 : 1) + kChunk * kRecW));
-      const int cur = k & 1;
-      bool ok = true;
-      int issued = 0;
-      for (int c = 0; c < NC; ++c) {
-        const unsigned g = cbase + (unsigned)c;
-        const int q = (int)(g % NST);
-        const unsigned use = g / NST;
-        if (use > 0 && !mbar_wait(&sm.empty[q], (use - 1) & 1)) { ok = false; break; }
-        const int l0 = chunk_l0(c);
-        mbar_expect_tx(&sm.full[q], bytes);
-        if (MODE == 0) tma_load_2d(&sm.tile[q][0][0], &maps.init, x0, st.lo + l0, &sm.full[q]);
-        else tma_load_2d(&sm.tile[q][0][0], &maps.state, x0, cur * X.rows + st.rowoff + l0, &sm.full[q]);
-        if (kUseForce) {
-          if (FMODE == 1) tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, dir * X.rows + st.rowoff + l0, &sm.full[q]);
-          else tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, st.lo + l0, &sm.full[q]);
-        }
-        tma_load_2d(&sm.rec[q][0][0], &maps.rec, 0, (s * 2 + dir) * X.Lpad + kRecPad + l0, &sm.full[q]);
-        ++issued;
-      }
-      if (!ok) {
-        atomicExch(X.flag, 1);
-        // drain: wait (bounded) for every stage that still has copies in flight
-        for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c) {
-          const unsigned g = cbase + (unsigned)c;
-          (void)mbar_wait(&sm.full[g % NST], (g / NST) & 1);
-        }
-        return false;
-      }
+  const int x0 = bx * (kWarpsPerBlock * kOutCols);
+  const unsigned bytes = (unsigned)(sizeof(T) * (kChunk * kBoxW * (kUseForce ? 2 : 1) + kChunk * kRecW));
+  const int cur = k & 1;
+  bool ok = true;
+  int issued = 0;
+  for (int c = 0; c < NC; ++c) {
+    const unsigned g = cbase + (unsigned)c;
+    const int q = (int)(g % NST);
+    const unsigned use = g / NST;
+    if (use > 0 && !mbar_wait(&sm.empty[q], (use - 1) & 1)) { ok = false; break; }
+    const int l0 = UP ? c * kChunk : L - (c + 1) * kChunk;
+    if (c == 0 && tail) {  // the unit's header, released to the consumers with the stage
+      static_assert(sizeof(TmaArgs<T>) % 4 == 0, "arguments are copied as 32-bit words");
+      sm.hdr[q].tail = *tail;
+      if (tail->new_args) copy_words(&sm.hdr[q].args, &X, (int)(sizeof(TmaArgs<T>) / 4), 0, 1);
     }
-    return true;
+    mbar_expect_tx(&sm.full[q], bytes);
+    if (MODE == 0) tma_load_2d(&sm.tile[q][0][0], &maps.init, x0, st.lo + l0, &sm.full[q]);
+    else tma_load_2d(&sm.tile[q][0][0], &maps.state, x0, cur * X.rows + st.rowoff + l0, &sm.full[q]);
+    if (kUseForce) {
+      if (FMODE == 1) tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, dir * X.rows + st.rowoff + l0, &sm.full[q]);
+      else tma_load_2d(&sm.frc[q][0][0], &maps.force, x0, st.lo + l0, &sm.full[q]);
+    }
+    tma_load_2d(&sm.rec[q][0][0], &maps.rec, 0, (s * 2 + dir) * X.Lpad + kRecPad + l0, &sm.full[q]);
+    ++issued;
   }
+  if (!ok) {
+    atomicExch(X.flag, 1);
+    // drain: wait (bounded) for every stage that still has copies in flight
+    for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c) {
+      const unsigned g = cbase + (unsigned)c;
+      (void)mbar_wait(&sm.full[g % NST], (g / NST) & 1);
+    }
+    return false;
+  }
+  return true;
+}
+
+// Consumer half of one unit's pass (the kWarpsPerBlock consumer warps).  ST: the
+// unit's strip from the stage header, or nullptr to read it from global memory.
+template <typename T, bool UP, int MODE, int FMODE, int NST>
+__device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, const int s, const int bx,
+                                             TmaSmem<T, NST>& sm, const unsigned cbase, const StripInfo* st_hdr) {
+  const PassArgs<T>& A = X.p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const StripInfo st = st_hdr ? *st_hdr : A.strips[s];
+  const int L = st.L;
+  const int NC = (L + kChunk - 1) / kChunk;
+  auto chunk_l0 = [&](int c) { return UP ? c * kChunk : L - (c + 1) * kChunk; };
 
   // ------------------------------ consumers ------------------------------
   const int wl = warp;
@@ -501,6 +536,21 @@ __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>&
   return true;
 }
 
+// One work unit: strip s, column block bx (4 warps = 120 output columns) of one
+// problem, for pass k.  Ring slots continue from chunk number cbase (so a block can
+// run several units back to back).  Returns false if a bounded wait expired.
+template <typename T, bool UP, int MODE, int FMODE, int NST>
+__device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
+                                          const int bx, TmaSmem<T, NST>& sm, const unsigned cbase) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kWarpsPerBlock) {
+    if (lane != 0) return true;
+    const StripInfo st = X.p.strips[s];
+    return produce_unit<T, UP, MODE, FMODE, NST>(maps, X, k, s, bx, st, sm, cbase, nullptr);
+  }
+  return consume_unit<T, UP, MODE, FMODE, NST>(X, k, s, bx, sm, cbase, nullptr);
+}
+
 // The dynamic shared-memory base is at least 16-byte aligned, which is what an
 // unswizzled TMA destination needs; using it directly (no integer round trip) keeps
 // every tile access a shared-memory load.
@@ -514,38 +564,56 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form: the nt-1 interior passes of an iteration in one launch.
+// Streamed form: the interior passes of an iteration in one persistent launch.
 // ---------------------------------------------------------------------------
 //
-// The first pass (elimination of step 1 from u^0) and the last (back-substitution
-// of step nt) stay launches of their own: inlining those two variants as well made
-// the FP64 kernel spill.
+// The interior passes (1 <= k < nt: back-substitution of step k fused with the
+// elimination of step k+1) of one or many problems are a list of tickets in pass
+// order: ticket t is unit t - pass_start[j] of pass k = 1 + j, where the units
+// (problem, strip s, column block bx) active in pass j are a prefix of the unit list
+// (problems sorted by decreasing nt).  A co-resident grid (cooperative launch)
+// draws tickets from one counter; each block's producer lane takes a ticket, waits
+// until the unit and its two column neighbours have finished the previous pass,
+// writes the unit's header into the stage of its first chunk and streams its
+// chunks; the consumer warps follow the stream of stages, reading each unit from
+// its header.  Pass k of a unit reads the residue of its own columns and of one
+// halo column on each side, written by the unit and its neighbours in pass k-1,
+// and overwrites the buffer they read in pass k-1; the wait covers both, and keeps
+// neighbours within one pass of each other, which the two residue buffers allow.
+// Tickets are taken in pass order, so every ticket a block waits on is held by a
+// running block: no cycle of waits.  The blocks' rings stay full across unit and
+// pass boundaries, so a unit's start-up latency hides behind the previous unit.
 //
-// The work of a pass is a list of units (strip s, column block bx); unit u = s * nbx
-// + bx.  Every block of a co-resident grid (cooperative launch) owns the units
-// blockIdx.x, blockIdx.x + gridDim.x, ... and walks them pass by pass, keeping its
-// TMA ring running across units and passes.  Pass k of unit u reads the residue
-// y^k of its own columns and of one halo column on each side, which the units u-1
-// and u+1 of the same strip wrote in pass k-1, and it overwrites the buffer those
-// units read in pass k-1.  So before the producer loads pass k of u it waits until
-// units u-1, u and u+1 have completed pass k-1; completion is a per-unit counter to
-// which every consumer warp adds one after its stores of a pass (no barrier inside
-// the block, so a warp that leaves on an error cannot strand the others).  Neighbours are then never more
-// than one pass apart, which is what the two residue buffers allow.  With one unit
-// per block the wait exposes one counter round trip per pass; with several, the
-// neighbours finished long before and the ring streams on.
-//
-// Every counter wait is bounded by wall time (globaltimer); on expiry, or when
-// another block has raised the error flag, the producer marks the ring aborted and
-// completes the next stage without data, so its consumers leave as well.
+// Completion of a unit's pass is a per-unit counter to which every consumer warp
+// adds one after its stores and a proxy fence (no barrier inside the block, so a
+// warp that leaves on an error cannot strand the others).  Every counter wait is
+// bounded by wall time (globaltimer); on expiry, or when another block has raised
+// the error flag, the producer marks the ring aborted and completes the next stage
+// without data, so that the consumers leave as well.
 
-struct PersistArgs {
-  unsigned* done;                 // [nunits] consumer warps x passes completed in this launch
-                                  // (zeroed before it)
-  int k_begin, k_end;             // passes k_begin .. k_end-1 (interior passes: 1 <= k < nt)
-  int nunits, nbx;                // units of the launch, column blocks per strip
-  int stall_unit;                 // self-test: this unit never reports completion (-1: none)
-  unsigned long long wait_ns;     // limit of one counter wait
+struct StreamUnit {
+  int inst, strip, bx, nc;  // problem, strip, column block, chunks of the strip
+  int left, right;          // list indices of the column neighbours (-1: none)
+};
+
+template <typename T>
+struct StreamProblem {
+  TmaMaps maps;    // 64-byte aligned tensor maps of this problem (global memory)
+  TmaArgs<T> args;
+  int nt, fmode;
+};
+
+struct StreamArgs {
+  const StreamUnit* units;       // sorted by decreasing nt of their problem
+  const int* pass_start;         // [npass + 1] first ticket of each interior pass
+  int npass;                     // interior passes of the longest problem (max nt - 1)
+  int dynamic;                   // 1: tickets from the counter; 0: block b runs unit b of every
+                                 // pass (the grid holds the largest pass)
+  unsigned* done;                // [units] consumer warps x passes completed (zeroed before)
+  unsigned* ticket;              // next ticket (zeroed before)
+  int* flag;                     // error flag (1 = a bounded wait expired)
+  int stall_unit;                // self-test: this unit never reports completion (-1: none)
+  unsigned long long wait_ns;    // limit of one counter wait
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -569,8 +637,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 // Bounded wait until done[a], done[b], done[c] (b, c may be -1) all reach target.
 // False on time-out (the error flag is raised) or when the error flag is already set.
-__device__ __forceinline__ bool wait_done(const PersistArgs& P, const int* err, int a, int b, int c,
-                                          unsigned target) {
+__device__ __forceinline__ bool wait_done(const StreamArgs& P, int a, int b, int c, unsigned target) {
   const unsigned long long t0 = global_ns();
   for (unsigned it = 0;; ++it) {
     bool ok = ld_acquire_u32(P.done + a) >= target;
@@ -578,109 +645,136 @@ __device__ __forceinline__ bool wait_done(const PersistArgs& P, const int* err, 
     if (c >= 0) ok = ok && ld_acquire_u32(P.done + c) >= target;
     if (ok) return true;
     if ((it & 15) == 15) {
-      if (*(volatile const int*)err) return false;
+      if (*(volatile const int*)P.flag) return false;
       if (global_ns() - t0 > P.wait_ns) {
-        atomicExch(const_cast<int*>(err), 1);
+        atomicExch(P.flag, 1);
         return false;
       }
     }
   }
 }
 
-// Interior pass k (back-substitution of step k, elimination of step k+1) of one
-// unit; pass k runs upward when k is even.
-template <typename T, int FMODE, int NST>
-__device__ __forceinline__ bool pass_unit_k(const TmaMaps& maps, const TmaArgs<T>& X, int k, int s, int bx,
-                                            TmaSmem<T, NST>& sm, unsigned cbase) {
-  return (k & 1) ? pass_unit<T, false, 1, FMODE, NST>(maps, X, k, s, bx, sm, cbase)
-                 : pass_unit<T, true, 1, FMODE, NST>(maps, X, k, s, bx, sm, cbase);
-}
-
 template <typename T, int FMODE, int NST>
 __global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
-sweep_persistent_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const PersistArgs P) {
+sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
   init_ring(sm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool producer = warp == kWarpsPerBlock;
   unsigned cbase = 0;
-  for (int k = P.k_begin; k < P.k_end; ++k) {
-    for (int u = blockIdx.x; u < P.nunits; u += gridDim.x) {
-      const int sl = u / P.nbx, bx = u - sl * P.nbx;
-      const int s = sl + X.p.strip0;
-      const int nc = (X.p.strips[s].L + kChunk - 1) / kChunk;
-      if (producer && lane == 0 && k > P.k_begin) {
-        const bool ok = wait_done(P, X.flag, u, bx > 0 ? u - 1 : -1, bx + 1 < P.nbx ? u + 1 : -1,
-                                  (unsigned)((k - P.k_begin) * kWarpsPerBlock));
-        if (!ok) {
-          // complete the next stage without data: the consumers see the abort word
-          sm.abort = 1;
-          const int q = (int)(cbase % NST);
-          const unsigned use = cbase / NST;
-          if (use == 0 || mbar_wait(&sm.empty[q], (use - 1) & 1)) mbar_arrive(&sm.full[q]);
-          return;
+  if (warp == kWarpsPerBlock) {
+    // ------------------------------ producer ------------------------------
+    if (lane != 0) return;
+    const unsigned total = (unsigned)P.pass_start[P.npass];
+    // next ticket: from the counter, or (static) unit blockIdx.x of the next pass
+    int j = 0, sj = -1;
+    auto next_ticket = [&]() -> unsigned {
+      if (P.dynamic) return atomicAdd(P.ticket, 1u);
+      ++sj;
+      if (sj >= P.npass) return total;
+      const unsigned t = (unsigned)P.pass_start[sj] + blockIdx.x;
+      return t < (unsigned)P.pass_start[sj + 1] ? t : total;  // pass sizes never grow
+    };
+    unsigned t = next_ticket();
+    int last_inst = -1;
+    for (;;) {
+      StreamTail h;
+      bool ok = true;
+      if (t >= total) {
+        h.k = -1;  // no more work
+      } else {
+        while ((unsigned)P.pass_start[j + 1] <= t) ++j;
+        const int u = (int)(t - (unsigned)P.pass_start[j]);
+        const StreamUnit un = P.units[u];
+        h.k = j + 1;
+        h.inst = un.inst;
+        h.strip = un.strip;
+        h.bx = un.bx;
+        h.nc = un.nc;
+        h.unit = u;
+        h.new_args = un.inst != last_inst;
+        last_inst = un.inst;
+        const StreamProblem<T>& pr = probs[un.inst];
+        h.st = pr.args.p.strips[un.strip];
+        if (j > 0) ok = wait_done(P, u, un.left, un.right, (unsigned)(j * kWarpsPerBlock));
+        if (ok) {
+          fence_proxy_async_global();
+          ok = (h.k & 1) ? produce_unit<T, false, 1, FMODE, NST>(pr.maps, pr.args, h.k, h.strip, h.bx, h.st, sm,
+                                                                 cbase, &h)
+                         : produce_unit<T, true, 1, FMODE, NST>(pr.maps, pr.args, h.k, h.strip, h.bx, h.st, sm,
+                                                                cbase, &h);
+          if (!ok) return;  // a ring wait expired; the consumers time out on their own
+          cbase += (unsigned)h.nc;
+          // the next ticket only now: a block that held two would sit on the second
+          // (possibly a pass ahead) while others run short of work
+          t = next_ticket();
+          continue;
         }
-        fence_proxy_async_global();
       }
-      const bool ok = pass_unit_k<T, FMODE, NST>(maps, X, k, s, bx, sm, cbase);
-      if (!ok) return;
-      if (!producer) {
-        // this warp's stores of pass k are visible (to loads and to TMA) before the
-        // unit's counter moves; each consumer warp adds one
-        __threadfence();
-        fence_proxy_async_global();
-        __syncwarp();
-        if (lane == 0 && u != P.stall_unit) red_release_add_u32(P.done + u, 1u);
+      // no more work, or a counter wait gave up: complete the next stage without
+      // data (after the consumers released it) so that the consumers leave
+      if (!ok) sm.abort = 1;
+      const int q = (int)(cbase % NST);
+      const unsigned use = cbase / NST;
+      if (use == 0 || mbar_wait(&sm.empty[q], (use - 1) & 1)) {
+        sm.hdr[q].tail.k = -1;
+        mbar_arrive(&sm.full[q]);
       }
-      cbase += (unsigned)nc;
+      return;
     }
+  }
+  // ------------------------------ consumers ------------------------------
+  for (;;) {
+    const int q = (int)(cbase % NST);
+    if (!mbar_wait(&sm.full[q], (cbase / NST) & 1)) {
+      atomicExch(P.flag, 1);
+      return;
+    }
+    if (*(volatile int*)&sm.abort) return;
+    if (sm.hdr[q].tail.k < 0) return;
+    // copy the header while the stage is held (its first chunk is not released yet);
+    // the pass arguments only when the problem changed (units come in the same order
+    // to every consumer warp, so the warp's copy holds the producer's last ones)
+    StreamHeader<T>& h = sm.cur[warp];
+    if (sm.hdr[q].tail.new_args) copy_words(&h.args, &sm.hdr[q].args, (int)(sizeof(TmaArgs<T>) / 4), lane, 32);
+    copy_words(&h.tail, &sm.hdr[q].tail, (int)(sizeof(StreamTail) / 4), lane, 32);
+    __syncwarp();
+    const int k = h.tail.k, s = h.tail.strip, bx = h.tail.bx, nc = h.tail.nc, u = h.tail.unit;
+    const bool ok = (k & 1) ? consume_unit<T, false, 1, FMODE, NST>(h.args, k, s, bx, sm, cbase, &h.tail.st)
+                            : consume_unit<T, true, 1, FMODE, NST>(h.args, k, s, bx, sm, cbase, &h.tail.st);
+    if (!ok) return;
+    // this warp's stores of the pass are visible (to loads and to TMA) before the
+    // unit's counter moves
+    __threadfence();
+    fence_proxy_async_global();
+    __syncwarp();
+    if (lane == 0 && u != P.stall_unit) red_release_add_u32(P.done + u, 1u);
+    cbase += (unsigned)nc;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Batched form: many independent problems in one launch per time step.
+// First and last passes of many units (one or many problems) in one launch.
 // ---------------------------------------------------------------------------
 
-struct BatchUnit {
-  int inst, strip, bx, nc;  // problem, strip, column block, chunks of the strip
-};
-
-template <typename T>
-struct BatchProblem {
-  TmaMaps maps;    // 64-byte aligned tensor maps of this problem (global memory)
-  TmaArgs<T> args;
-  int nt, fmode;
-};
-
-// Units u = blockIdx.x, blockIdx.x + gridDim.x, ...: with gridDim.x = number of units
-// every block runs one unit; with a smaller grid the blocks are persistent and walk
-// the list (sorted by decreasing work on the host).  The pass mode of a unit follows
-// from k and its problem's nt: 0 at k = 0, 2 at k = nt, skipped beyond.
-template <typename T, bool UP, int NST>
+// MODE 0: pass 0 (elimination of step 1 from u^0) of every listed unit; MODE 2: the
+// last pass (back-substitution of step nt, u^nt stored) of every listed unit, each
+// at its own problem's nt.  Units u = blockIdx.x, blockIdx.x + gridDim.x, ...: one
+// block per unit when the grid is as large as the list, persistent blocks otherwise.
+template <typename T, int MODE, int FMODE, int NST>
 __global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
-batch_pass_kernel(const BatchProblem<T>* __restrict__ probs, const BatchUnit* __restrict__ units, const int nunits,
-                  const int k) {
+edge_pass_kernel(const StreamProblem<T>* __restrict__ probs, const StreamUnit* __restrict__ units, const int nunits) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
   init_ring(sm);
   unsigned cbase = 0;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const BatchUnit un = units[u];
-    const BatchProblem<T>& bp = probs[un.inst];
-    const int nt = bp.nt;
-    if (k > nt) continue;
-    const int mode = (k == 0) ? 0 : (k == nt ? 2 : 1);
-    bool ok = true;
-#define KFP_UNIT(M, F) ok = pass_unit<T, UP, M, F, NST>(bp.maps, bp.args, k, un.strip, un.bx, sm, cbase)
-    if (mode == 1) {
-      if (bp.fmode == 1) KFP_UNIT(1, 1); else if (bp.fmode == 0) KFP_UNIT(1, 0); else KFP_UNIT(1, 2);
-    } else if (mode == 0) {
-      if (bp.fmode == 1) KFP_UNIT(0, 1); else if (bp.fmode == 0) KFP_UNIT(0, 0); else KFP_UNIT(0, 2);
-    } else {
-      KFP_UNIT(2, 0);  // the last pass reads no forcing
-    }
-#undef KFP_UNIT
+    const StreamUnit un = units[u];
+    const StreamProblem<T>& pr = probs[un.inst];
+    const int k = MODE == 0 ? 0 : pr.nt;
+    bool ok;
+    if (MODE == 0 || !(k & 1)) ok = pass_unit<T, true, MODE, FMODE, NST>(pr.maps, pr.args, k, un.strip, un.bx, sm, cbase);
+    else ok = pass_unit<T, false, MODE, FMODE, NST>(pr.maps, pr.args, k, un.strip, un.bx, sm, cbase);
     if (!ok) return;
     cbase += (unsigned)un.nc;
   }

@@ -250,9 +250,13 @@ struct kfp_swr {
   void* rec = nullptr;         // [S][2][Lpad][24] coefficient records
   int* flag = nullptr;         // device error flag (bounded waits)
   int use_tma = 0, fmode = 0, Lpad = 0;
-  // persistent sweep: one co-resident launch per iteration (per strip in the serial form)
+  // persistent (streamed) sweep: the interior passes of an iteration in one co-resident
+  // launch (one per strip in the serial form)
   int persist = 0, persist_grid = 0, nbx = 0;
-  unsigned* done = nullptr;    // [S * nbx] per-unit completion counters
+  unsigned* done = nullptr;    // [S * nbx] per-unit completion counters, then [S] tickets
+  void* sprob = nullptr;       // device StreamProblem<T> of this handle
+  kfp::StreamUnit* sunits = nullptr;  // [S * nbx], strip-major
+  int* spass = nullptr;        // [nt] first ticket of each interior pass (per group)
   int stall_unit = -1;         // self-test only
   unsigned long long wait_ns = 4000000000ull;
   kfp::TmaMaps maps;
@@ -322,6 +326,7 @@ struct kfp_swr {
   }
 
   size_t elem() const { return prec == KFP_F64 ? sizeof(double) : sizeof(float); }
+  int nbx_tma() const { return (g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock; }  // column blocks per strip
   int launches_per_iter() const {
     const int groups = (flags & KFP_FLAG_GAUSS_SEIDEL) ? g.S : 1;
     if (persist) return groups * (g.nt > 1 ? 3 : 2) + 2;
@@ -436,7 +441,8 @@ struct kfp_swr {
 
   // The persistent sweep, per group of strips (all strips; one strip at a time in the
   // serial form): the first pass, the nt-1 interior passes in one cooperative launch
-  // (after the units' completion counters are zeroed), the last pass.
+  // of the streamed kernel (after the units' counters and tickets are zeroed), the
+  // last pass.
   template <typename T, int FM>
   void enqueue_persistent(cudaStream_t st, bool interior_only = false) const {
     constexpr int NST = tma_stages<T>();
@@ -446,30 +452,34 @@ struct kfp_swr {
     const dim3 pgrid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
     const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
     const size_t smem = tma_smem_bytes<T>();
-    if (g.nt > 1) cudaMemsetAsync(done, 0, sizeof(unsigned) * (size_t)g.S * nbx, st);
+    if (g.nt > 1) cudaMemsetAsync(done, 0, sizeof(unsigned) * ((size_t)g.S * nbx + g.S), st);
     for (int grp = 0; grp < groups; ++grp) {
       X.p.strip0 = serial ? grp : 0;
       if (!interior_only) kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<pgrid, block, smem, st>>>(maps, X, 0);
-      if (g.nt > 1) enqueue_interior<T, FM>(st, X, serial);
+      if (g.nt > 1) enqueue_interior<T, FM>(st, serial ? grp : -1);
       if (interior_only) continue;
       if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
       else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
     }
   }
 
+  // Interior passes of all strips (strip < 0) or of one strip (serial form).
   template <typename T, int FM>
-  void enqueue_interior(cudaStream_t st, const kfp::TmaArgs<T>& X, bool serial) const {
+  void enqueue_interior(cudaStream_t st, int strip) const {
     constexpr int NST = tma_stages<T>();
-    kfp::PersistArgs P;
-    P.k_begin = 1;
-    P.k_end = g.nt;
-    P.nbx = nbx;
-    P.nunits = (serial ? 1 : g.S) * nbx;
-    P.done = done + (size_t)X.p.strip0 * nbx;
+    const int base = strip < 0 ? 0 : strip * nbx;
+    kfp::StreamArgs P;
+    P.units = sunits + base;
+    P.pass_start = spass;
+    P.npass = g.nt - 1;
+    P.dynamic = (strip < 0 ? g.S * nbx : nbx) > persist_grid ? 1 : 0;
+    P.done = done + base;
+    P.ticket = done + (size_t)g.S * nbx + (strip < 0 ? 0 : strip);
+    P.flag = flag;
     P.stall_unit = stall_unit;
     P.wait_ns = wait_ns;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)std::min(persist_grid, P.nunits));
+    cfg.gridDim = dim3((unsigned)persist_grid);
     cfg.blockDim = dim3((kfp::kWarpsPerBlock + 1) * 32);
     cfg.dynamicSmemBytes = tma_smem_bytes<T>();
     cfg.stream = st;
@@ -478,9 +488,8 @@ struct kfp_swr {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kfp::sweep_persistent_kernel<T, FM, NST>, maps, X, P);
+    cudaLaunchKernelEx(&cfg, kfp::sweep_stream_kernel<T, FM, NST>, (const kfp::StreamProblem<T>*)sprob, P);
   }
-
 
   template <typename T, int FM>
   void enqueue_passes_tma(cudaStream_t st) const {
@@ -522,16 +531,16 @@ struct kfp_swr {
     set((const void*)kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST>);
     set((const void*)kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST>);
     set((const void*)kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST>);
-    set((const void*)kfp::sweep_persistent_kernel<T, FM, NST>);
+    set((const void*)kfp::sweep_stream_kernel<T, FM, NST>);
     return e;
   }
 
-  // Blocks of the persistent sweep that fit on the device at once (0 if none).
+  // Blocks of the streamed sweep that fit on the device at once (0 if none).
   template <typename T, int FM>
   int persistent_capacity() const {
     constexpr int NST = tma_stages<T>();
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_persistent_kernel<T, FM, NST>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_stream_kernel<T, FM, NST>,
                                                       (kfp::kWarpsPerBlock + 1) * 32, tma_smem_bytes<T>()) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -813,7 +822,7 @@ struct kfp_swr {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    void* bufs[] = {Ybuf, GF, rec, flag, done, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
+    void* bufs[] = {Ybuf, GF, rec, flag, done, sprob, sunits, spass, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, zrec, fe_tab, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
     for (void* b : bufs)
@@ -1035,21 +1044,65 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
                                 : (h->fmode == 1 ? h->set_tma_smem_attr<T, 1>() : h->set_tma_smem_attr<T, 2>());
   if (e != cudaSuccess) return h->fail(KFP_ECUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
   h->use_tma = 1;
-  // Persistent sweep on request; periodic x needs its column wrap between passes and
-  // keeps one launch per pass.
-  if ((h->flags & KFP_FLAG_PERSISTENT) && !g.periodic) {
-    KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
-    const int cap = h->fmode == 0 ? h->persistent_capacity<T, 0>()
-                                  : (h->fmode == 1 ? h->persistent_capacity<T, 1>() : h->persistent_capacity<T, 2>());
+  // Streamed sweep when forced, or by default when a pass has more units than the
+  // device holds blocks at once (then it beats one launch per pass; below that the
+  // neighbour wait costs more than the launch it saves).  Periodic x needs its
+  // column wrap between passes and keeps one launch per pass.
+  KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
+  const int cap = h->fmode == 0 ? h->persistent_capacity<T, 0>()
+                                : (h->fmode == 1 ? h->persistent_capacity<T, 1>() : h->persistent_capacity<T, 2>());
+  const bool serial = (h->flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+  const int units_per_pass = (serial ? 1 : g.S) * h->nbx_tma();
+  const bool want = (h->flags & KFP_FLAG_PERSISTENT) ||
+                    (!(h->flags & KFP_FLAG_PER_PASS) && g.nt > 2 && units_per_pass > cap);
+  if (want && !g.periodic) {
     if (cap >= 1) {
-      h->nbx = (g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock;
-      rc = alloc(h, (void**)&h->done, sizeof(unsigned) * (size_t)g.S * h->nbx);
+      const int nbx = (g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock;
+      h->nbx = nbx;
+      const size_t nu = (size_t)g.S * nbx;
+      rc = alloc(h, (void**)&h->done, sizeof(unsigned) * (nu + g.S));
+      if (!rc) rc = alloc(h, (void**)&h->sunits, sizeof(kfp::StreamUnit) * nu);
+      if (!rc) rc = alloc(h, (void**)&h->spass, sizeof(int) * (size_t)std::max(g.nt, 1));
+      if (!rc) rc = alloc(h, &h->sprob, sizeof(kfp::StreamProblem<T>));
       if (rc) return rc;
-      KFP_CUDA_TRY_H(cudaMemset(h->done, 0, sizeof(unsigned) * (size_t)g.S * h->nbx));
+      KFP_CUDA_TRY_H(cudaMemset(h->done, 0, sizeof(unsigned) * (nu + g.S)));
+      // units strip-major; neighbour indices relative to the list a launch gets (the
+      // whole list, or one strip's part of it in the serial form)
+      std::vector<kfp::StreamUnit> su(nu);
+      for (int s = 0; s < g.S; ++s)
+        for (int bx = 0; bx < nbx; ++bx) {
+          kfp::StreamUnit& un = su[(size_t)s * nbx + bx];
+          const int rel = serial ? bx : s * nbx + bx;
+          un.inst = 0;
+          un.strip = s;
+          un.bx = bx;
+          un.nc = (g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk;
+          un.left = bx > 0 ? rel - 1 : -1;
+          un.right = bx + 1 < nbx ? rel + 1 : -1;
+        }
+      const int per_pass = serial ? nbx : (int)nu;
+      std::vector<int> ps((size_t)std::max(g.nt, 1));
+      for (size_t j = 0; j < ps.size(); ++j) ps[j] = (int)j * per_pass;
+      KFP_CUDA_TRY_H(cudaMemcpy(h->sunits, su.data(), sizeof(kfp::StreamUnit) * nu, cudaMemcpyHostToDevice));
+      KFP_CUDA_TRY_H(cudaMemcpy(h->spass, ps.data(), sizeof(int) * ps.size(), cudaMemcpyHostToDevice));
+      // h->sprob is written at the end of create, once every buffer it points to exists
       h->persist_grid = cap;
       h->persist = 1;
     }
   }
+  return KFP_OK;
+}
+
+// The streamed sweep's device copy of this problem's tensor maps and pass arguments.
+template <typename T>
+kfp_status upload_stream_problem(kfp_swr* h) {
+  kfp::StreamProblem<T> sp;
+  std::memset(&sp, 0, sizeof sp);
+  sp.maps = h->maps;
+  sp.args = h->tma_args<T>();
+  sp.nt = h->g.nt;
+  sp.fmode = h->fmode;
+  KFP_CUDA_TRY_H(cudaMemcpy(h->sprob, &sp, sizeof sp, cudaMemcpyHostToDevice));
   return KFP_OK;
 }
 
@@ -1222,6 +1275,7 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->scal, 0, sizeof(double) * 3, h->stream));
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream));
   KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->host_scal, sizeof(double) * 3));
+  if (h->persist) TRY(h->prec == KFP_F64 ? upload_stream_problem<double>(h) : upload_stream_problem<float>(h));
   for (auto& e : h->ev) KFP_CUDA_TRY_H(cudaEventCreate(&e));
   KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
   KFP_CUDA_TRY_H(cudaGetLastError());
@@ -1444,13 +1498,18 @@ struct kfp_batch {
   std::vector<kfp_swr*> inst;
   kfp_precision prec = KFP_F64;
   cudaStream_t stream = nullptr;
-  void* probs_dev = nullptr;
-  kfp::BatchUnit* units_dev = nullptr;
-  std::vector<kfp::BatchUnit> units;   // host copy, in launch order
-  std::vector<int> active_prefix;      // units active in pass k = prefix length
-  int max_nt = 0, sms = 1;
-  int blocks_per_sm = 0;               // 0: one block per unit; > 0: persistent grid
-  int unit_order = 0;                  // 0: by decreasing work; 1: round-robin over problems
+  void* probs_dev = nullptr;             // StreamProblem<T> per problem
+  kfp::StreamUnit* units_dev = nullptr;  // all units: grouped by forcing mode, each group in pass order
+  int* pass_dev = nullptr;               // per group: first ticket of each interior pass
+  unsigned* done = nullptr;              // [units] completion counters, then [3] tickets
+  std::vector<kfp::StreamUnit> units;    // host copy, in list order
+  int grp_begin[4] = {0, 0, 0, 0};       // forcing mode f: units [grp_begin[f], grp_begin[f+1])
+  int grp_npass[3] = {0, 0, 0};          // interior passes of group f (its longest problem's nt - 1)
+  int grp_pass_off[3] = {0, 0, 0};       // group f's pass table in pass_dev
+  int max_nt = 0, sms = 1, stream_grid = 0;
+  int blocks_per_sm = 0;               // first/last passes: 0 = one block per unit; > 0 persistent grid
+  int unit_order = 0;                  // within a pass: 0 = taller strips first; 1 = problem order
+  int* flag = nullptr;                 // error flag of the streamed launches
   long long iterations = 0, cells_per_iter = 0;
   double t_sweep = 0, t_reduce = 0;
   unsigned flags = 0;
@@ -1473,35 +1532,114 @@ struct kfp_batch {
   template <typename T>
   static constexpr int nst() { return kfp_swr::tma_stages<T>(); }
 
-  // Order the units: problems with more steps first (so the units of pass k are a
-  // prefix), then by decreasing work or round-robin over problems.
+  // List the units: by forcing mode (one streamed launch per mode), then by
+  // decreasing nt (the units of interior pass k are then a prefix of the group),
+  // then taller strips first or problem order.  Neighbour indices and the pass
+  // tables follow from the order.
   void order_units() {
-    std::stable_sort(units.begin(), units.end(), [&](const kfp::BatchUnit& a, const kfp::BatchUnit& b) {
+    std::stable_sort(units.begin(), units.end(), [&](const kfp::StreamUnit& a, const kfp::StreamUnit& b) {
+      const int fa = inst[a.inst]->fmode, fb = inst[b.inst]->fmode;
+      if (fa != fb) return fa < fb;
       const int na = inst[a.inst]->g.nt, nb = inst[b.inst]->g.nt;
       if (na != nb) return na > nb;
-      if (unit_order == 0) return a.nc > b.nc;
-      return false;
+      if (unit_order == 0 && a.nc != b.nc) return a.nc > b.nc;
+      if (a.inst != b.inst) return a.inst < b.inst;
+      if (a.strip != b.strip) return a.strip < b.strip;
+      return a.bx < b.bx;
     });
-    active_prefix.assign(max_nt + 1, 0);
-    for (int k = 0; k <= max_nt; ++k) {
-      int n = 0;
-      while (n < (int)units.size() && inst[units[n].inst]->g.nt >= k) ++n;
-      active_prefix[k] = n;
+    for (int f = 0; f <= 3; ++f) grp_begin[f] = 0;
+    for (const auto& u : units) grp_begin[inst[u.inst]->fmode + 1]++;
+    for (int f = 1; f <= 3; ++f) grp_begin[f] += grp_begin[f - 1];
+    // neighbour indices, relative to the group's first unit
+    std::vector<size_t> first(inst.size() + 1, 0);
+    for (size_t i = 0; i < inst.size(); ++i) first[i + 1] = first[i] + (size_t)inst[i]->g.S * inst[i]->nbx_tma();
+    std::vector<int> where(first.back(), -1);
+    for (size_t n = 0; n < units.size(); ++n) {
+      const auto& u = units[n];
+      where[first[u.inst] + (size_t)u.strip * inst[u.inst]->nbx_tma() + u.bx] = (int)n;
+    }
+    for (size_t n = 0; n < units.size(); ++n) {
+      auto& u = units[n];
+      const int base = grp_begin[inst[u.inst]->fmode], nbx = inst[u.inst]->nbx_tma();
+      const size_t row = first[u.inst] + (size_t)u.strip * nbx;
+      u.left = u.bx > 0 ? where[row + u.bx - 1] - base : -1;
+      u.right = u.bx + 1 < nbx ? where[row + u.bx + 1] - base : -1;
     }
   }
 
+  // Pass tables of the three groups, concatenated: group f's interior pass j holds
+  // the units whose problem has nt > j + 1.
+  std::vector<int> pass_tables() {
+    std::vector<int> all;
+    for (int f = 0; f < 3; ++f) {
+      int mx = 0;
+      for (int n = grp_begin[f]; n < grp_begin[f + 1]; ++n) mx = std::max(mx, inst[units[n].inst]->g.nt);
+      grp_npass[f] = std::max(mx - 1, 0);
+      grp_pass_off[f] = (int)all.size();
+      all.push_back(0);
+      for (int j = 0; j < grp_npass[f]; ++j) {
+        int active = 0;
+        for (int n = grp_begin[f]; n < grp_begin[f + 1]; ++n) active += inst[units[n].inst]->g.nt > j + 1 ? 1 : 0;
+        all.push_back(all.back() + active);
+      }
+    }
+    return all;
+  }
+
+  template <typename T, int FM>
+  void enqueue_group(cudaStream_t st, int mode) const {
+    constexpr int NST = nst<T>();
+    const size_t sm = kfp_swr::tma_smem_bytes<T>();
+    const auto* probs = (const kfp::StreamProblem<T>*)probs_dev;
+    const int n = grp_begin[FM + 1] - grp_begin[FM];
+    if (n == 0) return;
+    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
+    if (mode == 0) {
+      const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
+      kfp::edge_pass_kernel<T, 0, FM, NST><<<grid, block, sm, st>>>(probs, units_dev + grp_begin[FM], n);
+      return;
+    }
+    if (grp_npass[FM] == 0) return;
+    kfp::StreamArgs P;
+    P.units = units_dev + grp_begin[FM];
+    P.pass_start = pass_dev + grp_pass_off[FM];
+    P.npass = grp_npass[FM];
+    P.dynamic = n > stream_grid ? 1 : 0;  // the first pass is the largest
+    P.done = done + grp_begin[FM];
+    P.ticket = done + units.size() + FM;
+    P.flag = flag;
+    P.stall_unit = -1;
+    P.wait_ns = 4000000000ull;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)stream_grid);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kfp::sweep_stream_kernel<T, FM, NST>, probs, P);
+  }
+
+  // One iteration's passes: the first pass of every unit, the interior passes in one
+  // streamed launch per forcing mode, the last pass of every unit.
   template <typename T>
   void enqueue_passes(cudaStream_t st) const {
     constexpr int NST = nst<T>();
     const size_t sm = kfp_swr::tma_smem_bytes<T>();
-    const auto* probs = (const kfp::BatchProblem<T>*)probs_dev;
-    for (int k = 0; k <= max_nt; ++k) {
-      const int n = active_prefix[k];
-      if (n == 0) continue;
-      const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
-      if (k & 1) kfp::batch_pass_kernel<T, false, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(probs, units_dev, n, k);
-      else       kfp::batch_pass_kernel<T, true, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(probs, units_dev, n, k);
-    }
+    cudaMemsetAsync(done, 0, sizeof(unsigned) * (units.size() + 3), st);
+    enqueue_group<T, 0>(st, 0);
+    enqueue_group<T, 1>(st, 0);
+    enqueue_group<T, 2>(st, 0);
+    enqueue_group<T, 0>(st, 1);
+    enqueue_group<T, 1>(st, 1);
+    enqueue_group<T, 2>(st, 1);
+    const int n = (int)units.size();
+    const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
+    kfp::edge_pass_kernel<T, 2, 0, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(
+        (const kfp::StreamProblem<T>*)probs_dev, units_dev, n);
   }
 
   void enqueue_iteration(cudaStream_t st, bool capturing) const {
@@ -1527,10 +1665,15 @@ struct kfp_batch {
 
   kfp_status upload_units() {
     order_units();
+    const std::vector<int> tables = pass_tables();
     if (units_dev) cudaFree(units_dev);
+    if (pass_dev) cudaFree(pass_dev);
     units_dev = nullptr;
-    KFP_CUDA_TRY(cudaMalloc(&units_dev, sizeof(kfp::BatchUnit) * std::max<size_t>(units.size(), 1)));
-    KFP_CUDA_TRY(cudaMemcpy(units_dev, units.data(), sizeof(kfp::BatchUnit) * units.size(), cudaMemcpyHostToDevice));
+    pass_dev = nullptr;
+    KFP_CUDA_TRY(cudaMalloc(&units_dev, sizeof(kfp::StreamUnit) * std::max<size_t>(units.size(), 1)));
+    KFP_CUDA_TRY(cudaMemcpy(units_dev, units.data(), sizeof(kfp::StreamUnit) * units.size(), cudaMemcpyHostToDevice));
+    KFP_CUDA_TRY(cudaMalloc(&pass_dev, sizeof(int) * tables.size()));
+    KFP_CUDA_TRY(cudaMemcpy(pass_dev, tables.data(), sizeof(int) * tables.size(), cudaMemcpyHostToDevice));
     drop_graph();
     return KFP_OK;
   }
@@ -1598,6 +1741,9 @@ struct kfp_batch {
       r2 = h->check_flag();
       if (r2) return fail(r2, "%s", h->last_error.c_str());
     }
+    int f = 0;
+    KFP_CUDA_TRY(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) return fail(KFP_ETIMEOUT, "a bounded wait in the streamed sweep expired");
     iterations += done;
     if (iters_done) *iters_done = done;
     if (rc) return rc;
@@ -1612,6 +1758,9 @@ struct kfp_batch {
       if (e) cudaEventDestroy(e);
     if (probs_dev) cudaFree(probs_dev);
     if (units_dev) cudaFree(units_dev);
+    if (pass_dev) cudaFree(pass_dev);
+    if (done) cudaFree(done);
+    if (flag) cudaFree(flag);
     for (kfp_swr* h : inst) {
       if (!h) continue;
       cudaStreamSynchronize(h->stream);
@@ -1626,7 +1775,7 @@ namespace {
 
 template <typename T>
 kfp_status batch_setup(kfp_batch* b) {
-  std::vector<kfp::BatchProblem<T>> host(b->inst.size());
+  std::vector<kfp::StreamProblem<T>> host(b->inst.size());
   b->units.clear();
   b->max_nt = 0;
   b->cells_per_iter = 0;
@@ -1639,20 +1788,32 @@ kfp_status batch_setup(kfp_batch* b) {
     host[i].fmode = h->fmode;
     b->max_nt = std::max(b->max_nt, h->g.nt);
     b->cells_per_iter += h->g.cells_per_iter;
-    const int nbx = (h->g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock;
+    const int nbx = h->nbx_tma();
     for (int s = 0; s < h->g.S; ++s)
       for (int bx = 0; bx < nbx; ++bx)
-        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk});
+        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk, -1, -1});
   }
-  KFP_CUDA_TRY_ON(b, cudaMalloc(&b->probs_dev, sizeof(kfp::BatchProblem<T>) * host.size()));
-  KFP_CUDA_TRY_ON(b, cudaMemcpy(b->probs_dev, host.data(), sizeof(kfp::BatchProblem<T>) * host.size(),
+  KFP_CUDA_TRY_ON(b, cudaMalloc(&b->probs_dev, sizeof(kfp::StreamProblem<T>) * host.size()));
+  KFP_CUDA_TRY_ON(b, cudaMemcpy(b->probs_dev, host.data(), sizeof(kfp::StreamProblem<T>) * host.size(),
                           cudaMemcpyHostToDevice));
+  KFP_CUDA_TRY_ON(b, cudaMalloc(&b->done, sizeof(unsigned) * (b->units.size() + 3)));
+  KFP_CUDA_TRY_ON(b, cudaMalloc(&b->flag, sizeof(int)));
+  KFP_CUDA_TRY_ON(b, cudaMemset(b->flag, 0, sizeof(int)));
   constexpr int NST = kfp_batch::nst<T>();
   const int sm = (int)kfp_swr::tma_smem_bytes<T>();
-  KFP_CUDA_TRY_ON(b, cudaFuncSetAttribute((const void*)kfp::batch_pass_kernel<T, true, NST>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  KFP_CUDA_TRY_ON(b, cudaFuncSetAttribute((const void*)kfp::batch_pass_kernel<T, false, NST>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  auto attr = [&](const void* fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); };
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 0, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 1, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 2, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 2, 0, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 0, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 1, NST>));
+  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 2, NST>));
+  int per_sm = 0;
+  KFP_CUDA_TRY_ON(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_stream_kernel<T, 1, NST>,
+                                                                  (kfp::kWarpsPerBlock + 1) * 32, sm));
+  if (per_sm < 1) return b->fail(KFP_ECUDA, "the streamed sweep does not fit on an SM");
+  b->stream_grid = per_sm * b->sms;
   return b->upload_units();
 }
 

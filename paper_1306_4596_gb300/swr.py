@@ -25,6 +25,7 @@ KFP_F64, KFP_F32, KFP_MIXED = 0, 1, 2
 PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
 KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1, 2, 4, 8
 KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME, KFP_FLAG_PERSISTENT = 16, 32, 64, 128
+KFP_FLAG_PER_PASS = 256
 
 
 def problem_flags(prob) -> int:
@@ -388,7 +389,7 @@ class SWR:
     handed over and the library copies them in."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
-                 graph: bool = True, profile: bool = False, generic: bool = False, persistent: bool = False):
+                 graph: bool = True, profile: bool = False, generic: bool = False, persistent: Optional[bool] = None):
         import torch
 
         self.prob = prob
@@ -414,7 +415,8 @@ class SWR:
         self._p = np.ascontiguousarray(prob.p, dtype=np.float64) if S > 1 else None
         self._q = np.ascontiguousarray(prob.q, dtype=np.float64) if S > 1 else None
         flags = ((0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
-                 | (KFP_FLAG_GENERIC if generic else 0) | (KFP_FLAG_PERSISTENT if persistent else 0)
+                 | (KFP_FLAG_GENERIC if generic else 0)
+                 | {None: 0, True: KFP_FLAG_PERSISTENT, False: KFP_FLAG_PER_PASS}[persistent]
                  | problem_flags(prob))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,

@@ -54,6 +54,25 @@ def test_batch_equals_single_problem_runs(precision):
                 assert np.array_equal(hist, ref[i][2]), (bps, order, i)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_batch_units_as_long_as_the_ring(precision):
+    """Problems whose strips take exactly as many chunks as the ring has stages (4 in
+    FP64, 8 in FP32; 16 rows per chunk), so that a unit's successor starts in the
+    stage of the unit's own first chunk while that unit is still running, with
+    different problems (other arrays) back to back."""
+    from paper_1306_4596_gb300 import swr
+    rows = 60 if precision == "f64" else 120  # nv / S: strips of 61 or 121 rows, 4 or 8 chunks
+    probs = [RD(90 + 7 * i, rows * S, 5 + i, 0.002, S, 0, True, p=3.0 + i, seed=90 + i, nforce=1,
+                boundary_data=False) for i, S in enumerate((2, 3, 4, 2, 3))]
+    ref = [single_results(p, precision, 2) for p in probs]
+    with swr.Batch(probs, precision) as b:
+        b.sweep(2)
+        for i in range(len(probs)):
+            v = b.view(i)
+            assert np.array_equal(v.solution(), ref[i][0]), i
+            assert np.array_equal(v.traces(), ref[i][1]), i
+
+
 def test_batch_matches_oracle():
     from paper_1306_4596_gb300 import swr
     probs = batch_problems()
