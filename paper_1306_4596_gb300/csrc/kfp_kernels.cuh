@@ -269,16 +269,30 @@ __device__ __forceinline__ bool last_block_combine(double* partial, unsigned* ti
 }
 
 // Exchange: lam_in <- lam_next, e_chg = max |lam_next - lam_in| (trace change).
+// n is even (the data come in pairs of sides), so the arrays are read as 16-byte
+// pairs; four pairs per thread and round are in flight at once.
 __global__ void __launch_bounds__(kReduceThreads)
 exchange_kernel(const double* __restrict__ lam_next, double* __restrict__ lam_in, size_t n,
                 double* partial, unsigned* ticket, double* scal) {
   double mx = 0.0, sm = 0.0;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const double nv = lam_next[e];
-    const double d = fabs(nv - lam_in[e]);
-    mx = nan_max(mx, d);
-    lam_in[e] = nv;
+  const double2* __restrict__ nx2 = reinterpret_cast<const double2*>(lam_next);
+  double2* __restrict__ in2 = reinterpret_cast<double2*>(lam_in);
+  const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n2; e += 4 * stride) {
+    double2 a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { a[r] = nx2[e + r * stride]; b[r] = in2[e + r * stride]; }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      mx = nan_max(mx, nan_max(fabs(a[r].x - b[r].x), fabs(a[r].y - b[r].y)));
+      in2[e + r * stride] = a[r];
+    }
+  }
+  for (; e < n2; e += stride) {
+    const double2 a = nx2[e], b = in2[e];
+    mx = nan_max(mx, nan_max(fabs(a.x - b.x), fabs(a.y - b.y)));
+    in2[e] = a;
   }
   block_reduce(mx, sm);
   last_block_combine(partial, ticket, mx, sm, &scal[1], nullptr);
@@ -327,7 +341,10 @@ __global__ void correct_kernel(double* __restrict__ lam_in, const double* __rest
 }
 
 // Error: e_mis = max |lower - upper| over the overlaps, j_l2 = dt hx sum (lower-upper)^2.
-// Also appends (e_mis, e_chg, j_l2) to the device history.
+// Also appends (e_mis, e_chg, j_l2) to the device history.  Element e = j per_side + r
+// of the flat range pairs bands[j][0][r] with bands[j][1][r]; the thread's position
+// is advanced by the grid stride instead of being divided out per element, and four
+// elements per thread and round are in flight at once.
 __global__ void __launch_bounds__(kReduceThreads)
 error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double dthx,
              double* partial, unsigned* ticket, double* scal, double* hist, int* iter,
@@ -335,13 +352,56 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
   // wrap_nxp = nx + 1 with periodic x (column nx repeats column 0 and is left out of
   // the L2 sum), 0 otherwise
   double mx = 0.0, sm = 0.0;
-  const size_t n = (size_t)nif * per_side;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = e / per_side, r = e - j * per_side;
-    const double d = bands[(j * 2 + 0) * per_side + r] - bands[(j * 2 + 1) * per_side + r];
+  const size_t n = (size_t)nif * per_side, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t e0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // per_side is a multiple of the row length, so the column of e is e mod (nx + 1)
+  const size_t sj = stride / per_side, sr = stride - sj * per_side;
+  const int scol = wrap_nxp ? (int)(stride % (size_t)wrap_nxp) : 0;
+  struct Pos {
+    size_t lo;  // index of bands[j][0][r]; bands[j][1][r] is lo + per_side
+    size_t r;
+    int m;
+  };
+  auto advance = [&](Pos p) {
+    const size_t r2 = p.r + sr;
+    const size_t wrap = r2 >= per_side ? 1 : 0;
+    p.lo += (2 * (sj + wrap)) * per_side + sr - wrap * per_side;
+    p.r = r2 - wrap * per_side;
+    if (wrap_nxp) {
+      p.m += scol;
+      if (p.m >= wrap_nxp) p.m -= wrap_nxp;
+    }
+    return p;
+  };
+  Pos p;
+  {
+    const size_t j = e0 / per_side;
+    p.r = e0 - j * per_side;
+    p.lo = 2 * j * per_side + p.r;
+    p.m = wrap_nxp ? (int)(e0 % (size_t)wrap_nxp) : 0;
+  }
+  size_t e = e0;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    Pos q[4];
+    q[0] = p;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) q[k] = advance(q[k - 1]);
+    double lo[4], up[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { lo[k] = bands[q[k].lo]; up[k] = bands[q[k].lo + per_side]; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double d = lo[k] - up[k];
+      mx = nan_max(mx, fabs(d));
+      if (wrap_nxp == 0 || q[k].m != wrap_nxp - 1) sm += d * d;
+    }
+    p = advance(q[3]);
+  }
+  for (; e < n; e += stride) {
+    const double d = bands[p.lo] - bands[p.lo + per_side];
     mx = nan_max(mx, fabs(d));
-    if (wrap_nxp == 0 || (int)(r % (size_t)wrap_nxp) != wrap_nxp - 1) sm += d * d;
+    if (wrap_nxp == 0 || p.m != wrap_nxp - 1) sm += d * d;
+    p = advance(p);
   }
   block_reduce(mx, sm);
   double emis = 0.0, ssum = 0.0;
