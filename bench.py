@@ -497,7 +497,8 @@ def main():
                 batched[prec] = {"value": bcells * nsteps / (bms / 1e3), "unit": UNIT, "steps": nsteps,
                                  "ms_per_step": bms / nsteps,
                                  "launch_shape": {"blocks_per_sm": tuned["blocks_per_sm"],
-                                                  "unit_order": tuned["unit_order"]},
+                                                  "unit_order": tuned["unit_order"],
+                                                  "tile_shape": tuned["tile_shape"]},
                                  "candidates_ms": [round(c["ms"], 2) for c in tuned["candidates"]]}
             del batch_probs
             line["batched"] = batched

@@ -89,6 +89,14 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
  * blocks at once, and one launch per pass otherwise (measured faster there). */
 #define KFP_FLAG_PERSISTENT 128u /* always the streamed sweep */
 #define KFP_FLAG_PER_PASS 256u   /* always one launch per pass */
+/* Tile shape of the TMA-fed sweep (rows per ring stage, ring stages, blocks per SM);
+ * results are bitwise the same for every shape.  By default the library takes shape
+ * 0 when a pass has at most one unit per SM and shape 1 otherwise.
+ *   KFP_FLAG_SHAPE(0): 16-row stages, 1 block per SM (4 stages FP64, 8 FP32)
+ *   KFP_FLAG_SHAPE(1):  8-row stages, 2 blocks per SM (4 stages FP64, 8 FP32)
+ *   KFP_FLAG_SHAPE(2):  8-row stages, 2 blocks per SM (6 stages FP64, 12 FP32) */
+#define KFP_FLAG_SHAPE_SHIFT 9
+#define KFP_FLAG_SHAPE(n) ((unsigned)((n) + 1) << KFP_FLAG_SHAPE_SHIFT)
 #define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each
                                   * step (M + dt S) w = M (u^n + dt f^{n+1}) with P1 elements in v
                                   * (mass M, stiffness S; Robin ends add dt p or dt q to the end row
@@ -305,10 +313,13 @@ kfp_status kfp_swr_counters(kfp_swr_t h, long long* fp64_iterations, long long* 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent problems (uneven grids, strip counts, Robin
  * parameters and step counts) swept together.  Every time step of every problem is
- * one work unit per (strip, block of 120 columns); one launch per time step runs the
- * units of all problems that have that step, and one iteration (all launches plus
- * the per-problem exchange and error reductions) replays as one CUDA graph.  The
- * method per problem is exactly that of kfp_swr_sweep (Section 6.3, parallel form).
+ * one work unit per (strip, block of 120 columns).  Per iteration: one launch runs the
+ * first pass of every unit; one persistent (cooperative) launch per forcing mode runs
+ * all interior passes of all problems, units taking work in pass order and waiting
+ * (bounded) on their column neighbours; one launch runs the last pass of every unit;
+ * then the per-problem exchange and error reductions.  The iteration replays as one
+ * CUDA graph.  The method per problem is exactly that of kfp_swr_sweep (Section 6.3,
+ * parallel form), and every problem's results equal its single-problem run bit for bit.
  * ------------------------------------------------------------------------- */
 typedef struct kfp_batch* kfp_batch_t;
 
@@ -319,11 +330,13 @@ typedef struct kfp_batch* kfp_batch_t;
 kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* probs, int count, void* cuda_stream,
                             kfp_batch_t* out);
 
-/* Launch shape: blocks_per_sm = 0 runs one block per work unit; > 0 runs a persistent
- * grid of blocks_per_sm x (number of SMs) blocks that walk the unit list.  unit_order
- * 0 lists the units of each step count by decreasing work, 1 keeps problem order.
- * Results do not depend on either choice.  Synchronises.  Errors: KFP_EINVAL. */
-kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order);
+/* Launch shape.  blocks_per_sm (first and last passes): 0 runs one block per work
+ * unit, > 0 a grid of blocks_per_sm x (number of SMs) blocks that walk the unit list.
+ * unit_order: 0 lists the units of each step count taller strips first, 1 keeps
+ * problem order.  tile_shape (interior passes): the shapes of KFP_FLAG_SHAPE, 0..2
+ * (default 1).  Results do not depend on any choice.  Synchronises.  Errors:
+ * KFP_EINVAL, KFP_ECUDA. */
+kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order, int tile_shape);
 
 /* Run iterations of every problem, as kfp_swr_sweep; with tol > 0 stop when every
  * problem's chosen norm is below tol. */

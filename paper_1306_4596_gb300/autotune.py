@@ -1,15 +1,18 @@
 """Launch-shape autotuner for the batched sweep.
 
-The batched sweep has two launch knobs that do not change results:
-``blocks_per_sm`` (0 = one block per work unit, the hardware block scheduler
-balances the load; k > 0 = a persistent grid of k blocks per SM walking the unit
-list) and ``unit_order`` (units of each step count by decreasing work, or in
-problem order).  ``tune`` times one SWR iteration of the actual batch for every
-candidate with CUDA events on the batch's stream and keeps the fastest; the choice
-is cached per batch signature (precision and the sorted problem shapes) in a JSON
-file under ``$KFP_SWR_CACHE`` (default ``~/.cache/kfp_swr``), so a later batch of
-the same shapes skips the timing.  Tuning iterations are real SWR iterations of
-the batch (they advance it).
+The batched sweep has three knobs that do not change results:
+``tile_shape`` of the streamed interior passes (0: 16-row ring stages and one block
+per SM; 1: 8-row stages, two blocks per SM; 2: the same with a deeper ring -- see
+kfp_launch.h), ``unit_order`` (units of each step count taller strips first, or in
+problem order) and ``blocks_per_sm`` of the first and last passes (0 = one block per
+work unit, the hardware block scheduler balances the load; k > 0 = k blocks per SM
+walking the unit list).  ``tune`` times one SWR iteration of the actual batch for
+every candidate (after one untimed iteration that captures its CUDA graph) with
+CUDA events on the batch's stream and keeps the fastest; the choice is cached per
+batch signature (precision and the sorted problem shapes) in a JSON file under
+``$KFP_SWR_CACHE`` (default ``~/.cache/kfp_swr``), so a later batch of the same
+shapes skips the timing.  Tuning iterations are real SWR iterations of the batch
+(they advance it).
 """
 from __future__ import annotations
 
@@ -18,7 +21,9 @@ import json
 import os
 from typing import Dict, Iterable, Optional, Tuple
 
-CANDIDATES: Tuple[Tuple[int, int], ...] = ((0, 0), (0, 1), (1, 0), (1, 1))
+# (blocks_per_sm, unit_order, tile_shape)
+CANDIDATES: Tuple[Tuple[int, int, int], ...] = tuple(
+    (bps, order, shape) for shape in (1, 2, 0) for order in (0, 1) for bps in (0, 1))
 
 
 def cache_path() -> str:
@@ -49,32 +54,33 @@ def _store_cache(cache: Dict[str, dict]) -> None:
     os.replace(tmp, path)
 
 
-def tune(batch, precision: str, candidates: Iterable[Tuple[int, int]] = CANDIDATES, use_cache: bool = True,
+def tune(batch, precision: str, candidates: Iterable[Tuple[int, int, int]] = CANDIDATES, use_cache: bool = True,
          repeats: int = 1) -> dict:
-    """Pick and apply the fastest (blocks_per_sm, unit_order) for this batch."""
+    """Pick and apply the fastest (blocks_per_sm, unit_order, tile_shape) for this batch."""
     import torch
 
     key = signature(batch.probs, precision)
     cache = _load_cache() if use_cache else {}
     if key in cache:
         best = cache[key]
-        batch.configure(best["blocks_per_sm"], best["unit_order"])
+        batch.configure(best["blocks_per_sm"], best["unit_order"], best.get("tile_shape", 1))
         return {**best, "cached": True}
     stream = batch.stream
     timings = []
-    for bps, order in candidates:
-        batch.configure(bps, order)
+    for bps, order, shape in candidates:
+        batch.configure(bps, order, shape)
         batch.sweep(1)  # graph capture and warm-up
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
         batch.sweep(repeats)
         end.record(stream)
         end.synchronize()
-        timings.append({"blocks_per_sm": bps, "unit_order": order, "ms": start.elapsed_time(end) / repeats})
+        timings.append({"blocks_per_sm": bps, "unit_order": order, "tile_shape": shape,
+                        "ms": start.elapsed_time(end) / repeats})
     best = min(timings, key=lambda t: t["ms"])
-    batch.configure(best["blocks_per_sm"], best["unit_order"])
-    result = {"blocks_per_sm": best["blocks_per_sm"], "unit_order": best["unit_order"], "ms": best["ms"],
-              "candidates": timings}
+    batch.configure(best["blocks_per_sm"], best["unit_order"], best["tile_shape"])
+    result = {"blocks_per_sm": best["blocks_per_sm"], "unit_order": best["unit_order"],
+              "tile_shape": best["tile_shape"], "ms": best["ms"], "candidates": timings}
     if use_cache:
         cache[key] = result
         _store_cache(cache)

@@ -1,8 +1,9 @@
 """Build the sm_103a shared library ``_build/libkfp_swr.so`` with nvcc.
 
-Translation units (``csrc/kfp_swr.cu``, which includes the kernels,
-``csrc/kfp_noalloc.cu`` and ``csrc/kfp_probe.cu``) are compiled to objects in
-parallel, one ``-gencode`` (compute_103a / sm_103a), then linked; built in-tree
+Translation units (``csrc/kfp_swr.cu`` with the host driver and the other kernels,
+``csrc/kfp_launch_<precision>_s<shape>.cu`` with the TMA-fed sweep kernels of one
+precision and tile shape each, ``csrc/kfp_noalloc.cu`` and ``csrc/kfp_probe.cu``) are
+compiled to objects in parallel, one ``-gencode`` (compute_103a / sm_103a), then linked; built in-tree
 so that the process loading it is seen using it.  Host code is compiled without
 floating-point contraction so that its setup arithmetic (grid nodes, factors)
 rounds the same on x86 and Arm.
@@ -18,7 +19,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkfp_swr.so")
-SOURCES = [os.path.join(CSRC, "kfp_swr.cu"), os.path.join(CSRC, "kfp_noalloc.cu"), os.path.join(CSRC, "kfp_probe.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in (
+    "kfp_swr.cu", "kfp_noalloc.cu", "kfp_probe.cu",
+    # the TMA-fed sweep kernels, one precision and tile shape per translation unit
+    "kfp_launch_f64_s0.cu", "kfp_launch_f64_s1.cu", "kfp_launch_f64_s2.cu",
+    "kfp_launch_f32_s0.cu", "kfp_launch_f32_s1.cu", "kfp_launch_f32_s2.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, "kfp_swr.h")]
 

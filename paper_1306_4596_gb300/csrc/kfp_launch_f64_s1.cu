@@ -1,0 +1,4 @@
+// Sweep kernels of one precision and tile shape (see kfp_launch.h): double, shape 1.
+#include "kfp_launch.cuh"
+
+KFP_INSTANTIATE_LAUNCH(double, 1)

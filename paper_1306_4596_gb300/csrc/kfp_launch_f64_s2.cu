@@ -1,0 +1,4 @@
+// Sweep kernels of one precision and tile shape (see kfp_launch.h): double, shape 2.
+#include "kfp_launch.cuh"
+
+KFP_INSTANTIATE_LAUNCH(double, 2)

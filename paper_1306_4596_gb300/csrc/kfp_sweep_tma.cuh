@@ -5,10 +5,10 @@
 // upwind neighbour, halo lanes), but every per-row input is streamed into shared
 // memory by the tensor-memory accelerator ahead of use:
 //
-//   warp 4 (producer, one elected lane) issues, per chunk of kChunk rows,
-//     cp.async.bulk.tensor.2d loads of the block's [kChunk x kBoxW] tile of the
+//   warp 4 (producer, one elected lane) issues, per chunk of CH rows,
+//     cp.async.bulk.tensor.2d loads of the block's [CH x kBoxW] tile of the
 //     elimination residue y^k (or u^0 in the first pass), the same tile of the
-//     forcing term, and the [kChunk x 24] tile of per-row coefficient records,
+//     forcing term, and the [CH x 24] tile of per-row coefficient records,
 //   into a ring of NST stages guarded by full/empty mbarriers;
 //   warps 0..3 (consumers) wait on the stage, run the row recurrences from shared
 //     memory and store y^{k+1} straight to global memory (coalesced).
@@ -42,10 +42,21 @@
 
 namespace kfp {
 
-constexpr int kChunk = 16;                                   // rows per stage
+constexpr int kChunkMax = 16;                                // most rows per stage (record padding)
+
+// Tile shape of the TMA-fed sweep: CH rows per ring stage (8 or 16), NST ring stages,
+// MINB blocks resident per SM (the launch bound).  16-row stages and one block per
+// SM suit a pass with about one unit per SM; 8-row stages need fewer registers and
+// less shared memory, so that two blocks -- two consumer warps per SM sub-partition
+// -- hide each other's latencies when a pass has several units per SM.
+template <int CH_, int NST_, int MINB_>
+struct Shape {
+  static constexpr int CH = CH_, NST = NST_, MINB = MINB_;
+  static_assert(CH == 8 || CH == 16, "tensor maps exist for 8- and 16-row boxes");
+};
 constexpr int kBoxW = kWarpsPerBlock * kOutCols + 4;         // 124 columns per tile
 constexpr int kRecW = 24;                                    // record row: 3 classes x 8
-constexpr int kRecPad = kChunk;                              // zero rows before/after each record table
+constexpr int kRecPad = kChunkMax;                           // zero rows before/after each record table
 constexpr unsigned kSpinLimit = 1u << 26;                    // bounded mbarrier waits
 
 struct TmaMaps {
@@ -125,14 +136,14 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, int n, in
   for (int i = lane; i < n; i += lanes) d[i] = s[i];
 }
 
-template <typename T, int NST>
+template <typename T, class SH>
 struct TmaSmem {
-  T tile[NST][kChunk][kBoxW];
-  T frc[NST][kChunk][kBoxW];
-  T rec[NST][kChunk][kRecW];
-  uint64_t full[NST];
-  uint64_t empty[NST];
-  StreamHeader<T> hdr[NST];
+  T tile[SH::NST][SH::CH][kBoxW];
+  T frc[SH::NST][SH::CH][kBoxW];
+  T rec[SH::NST][SH::CH][kRecW];
+  uint64_t full[SH::NST];
+  uint64_t empty[SH::NST];
+  StreamHeader<T> hdr[SH::NST];
   // each consumer warp's copy of the header of the unit it is running: once the
   // unit's first stage is released, a later unit's header may land in that stage
   StreamHeader<T> cur[kWarpsPerBlock];
@@ -224,10 +235,10 @@ __device__ __forceinline__ T special_row(const PassArgs<T>& A, int kind, int k1,
 // MODE 0: eliminate step 1 from u^0; 1: back-substitute step k, eliminate step k+1;
 // 2: back-substitute the last step and store u^nt.  FMODE: 0 no forcing, 1 folded
 // constant forcing, 2 one time-dependent term.
-template <typename T, int NST>
-__device__ __forceinline__ void init_ring(TmaSmem<T, NST>& sm) {
+template <typename T, class SH>
+__device__ __forceinline__ void init_ring(TmaSmem<T, SH>& sm) {
   if (threadIdx.x == 0) {
-    for (int q = 0; q < NST; ++q) {
+    for (int q = 0; q < SH::NST; ++q) {
       mbar_init(&sm.full[q], 1);
       mbar_init(&sm.empty[q], kWarpsPerBlock);
     }
@@ -242,25 +253,25 @@ __device__ __forceinline__ void init_ring(TmaSmem<T, NST>& sm) {
 // header (and, when tail->new_args, a copy of X) into the stage of the first chunk
 // before that stage is released.  Returns false if a
 // bounded wait expired (the copies already issued are drained first).
-template <typename T, bool UP, int MODE, int FMODE, int NST>
+template <typename T, bool UP, int MODE, int FMODE, class SH>
 __device__ __forceinline__ bool produce_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
-                                             const int bx, const StripInfo& st, TmaSmem<T, NST>& sm,
+                                             const int bx, const StripInfo& st, TmaSmem<T, SH>& sm,
                                              const unsigned cbase, const StreamTail* tail) {
   const int L = st.L;
-  const int NC = (L + kChunk - 1) / kChunk;
+  const int NC = (L + SH::CH - 1) / SH::CH;
   constexpr bool kUseForce = (MODE != 2) && (FMODE != 0);
   const int dir = UP ? 0 : 1;
   const int x0 = bx * (kWarpsPerBlock * kOutCols);
-  const unsigned bytes = (unsigned)(sizeof(T) * (kChunk * kBoxW * (kUseForce ? 2 : 1) + kChunk * kRecW));
+  const unsigned bytes = (unsigned)(sizeof(T) * (SH::CH * kBoxW * (kUseForce ? 2 : 1) + SH::CH * kRecW));
   const int cur = k & 1;
   bool ok = true;
   int issued = 0;
   for (int c = 0; c < NC; ++c) {
     const unsigned g = cbase + (unsigned)c;
-    const int q = (int)(g % NST);
-    const unsigned use = g / NST;
+    const int q = (int)(g % SH::NST);
+    const unsigned use = g / SH::NST;
     if (use > 0 && !mbar_wait(&sm.empty[q], (use - 1) & 1)) { ok = false; break; }
-    const int l0 = UP ? c * kChunk : L - (c + 1) * kChunk;
+    const int l0 = UP ? c * SH::CH : L - (c + 1) * SH::CH;
     if (c == 0 && tail) {  // the unit's header, released to the consumers with the stage
       static_assert(sizeof(TmaArgs<T>) % 4 == 0, "arguments are copied as 32-bit words");
       sm.hdr[q].tail = *tail;
@@ -279,9 +290,9 @@ __device__ __forceinline__ bool produce_unit(const TmaMaps& maps, const TmaArgs<
   if (!ok) {
     atomicExch(X.flag, 1);
     // drain: wait (bounded) for every stage that still has copies in flight
-    for (int c = (issued > NST ? issued - NST : 0); c < issued; ++c) {
+    for (int c = (issued > SH::NST ? issued - SH::NST : 0); c < issued; ++c) {
       const unsigned g = cbase + (unsigned)c;
-      (void)mbar_wait(&sm.full[g % NST], (g / NST) & 1);
+      (void)mbar_wait(&sm.full[g % SH::NST], (g / SH::NST) & 1);
     }
     return false;
   }
@@ -290,15 +301,15 @@ __device__ __forceinline__ bool produce_unit(const TmaMaps& maps, const TmaArgs<
 
 // Consumer half of one unit's pass (the kWarpsPerBlock consumer warps).  ST: the
 // unit's strip from the stage header, or nullptr to read it from global memory.
-template <typename T, bool UP, int MODE, int FMODE, int NST>
+template <typename T, bool UP, int MODE, int FMODE, class SH>
 __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, const int s, const int bx,
-                                             TmaSmem<T, NST>& sm, const unsigned cbase, const StripInfo* st_hdr) {
+                                             TmaSmem<T, SH>& sm, const unsigned cbase, const StripInfo* st_hdr) {
   const PassArgs<T>& A = X.p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const StripInfo st = st_hdr ? *st_hdr : A.strips[s];
   const int L = st.L;
-  const int NC = (L + kChunk - 1) / kChunk;
-  auto chunk_l0 = [&](int c) { return UP ? c * kChunk : L - (c + 1) * kChunk; };
+  const int NC = (L + SH::CH - 1) / SH::CH;
+  auto chunk_l0 = [&](int c) { return UP ? c * SH::CH : L - (c + 1) * SH::CH; };
 
   // ------------------------------ consumers ------------------------------
   const int wl = warp;
@@ -350,12 +361,12 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
   // FMA chains keep the FP64 pipe busy.  Its inputs live in registers, so its
   // shared-memory stage is already released.
   bool pend = false;
-  T xx[kChunk], hn[kChunk];
+  T xx[SH::CH], hn[SH::CH];
   T* pout = nullptr;
   auto drain = [&]() {
     T y_last = T(0);
 #pragma unroll
-    for (int t = 0; t < kChunk; ++t) {
+    for (int t = 0; t < SH::CH; ++t) {
       if (t > 0 && out_lane) *pout = y_last;
       if (t > 0) pout += step;
       y_prev = fma(hn[t], y_prev, xx[t]);
@@ -367,14 +378,14 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
   };
   for (int c = 0; c < NC; ++c) {
     const unsigned g = cbase + (unsigned)c;
-    const int q = (int)(g % NST);
-    if (!mbar_wait(&sm.full[q], (g / NST) & 1)) {
+    const int q = (int)(g % SH::NST);
+    if (!mbar_wait(&sm.full[q], (g / SH::NST) & 1)) {
       atomicExch(X.flag, 1);
       return false;
     }
     if (*(volatile int*)&sm.abort) return false;  // the producer gave up (stage holds no data)
     const int l0 = chunk_l0(c);
-    const int l1 = l0 + kChunk - 1;
+    const int l1 = l0 + SH::CH - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
                                            (rloT <= rhiT && !(l1 < rloT || l0 > rhiT)));
     // Chunks that reach outside the strip, caller boundary data, and chunks in which
@@ -385,21 +396,21 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
     // either end of a chunk has no transport (its upwind coefficient is 0), so it takes
     // the chunk's neighbour lane like the other rows.
     const int sg_first = slot_int(sm.rec[q][0][cls * 8 + 6]);
-    const int sg_last = slot_int(sm.rec[q][kChunk - 1][cls * 8 + 6]);
+    const int sg_last = slot_int(sm.rec[q][SH::CH - 1][cls * 8 + 6]);
     const bool general = X.bc_data || l0 < 0 || l1 >= L || sg_first * sg_last < 0;
     if (!general) {
       // upwind neighbour lane for the whole chunk
       const int src = lane - (sg_first != 0 ? sg_first : sg_last);
-      const int lf = UP ? l0 : l0 + kChunk - 1;  // first row in pass order
+      const int lf = UP ? l0 : l0 + SH::CH - 1;  // first row in pass order
       const int cbase = wl * kOutCols + lane;
       // (A) back-substitution chain of this chunk, interleaved with the deferred
       //     elimination chain of the previous chunk
-      T uu[kChunk];
+      T uu[SH::CH];
       constexpr bool kLateStore = sizeof(T) == 4;  // measured: helps FP32, not FP64
       if (pend && !kLateStore) {
 #pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
-          const int r = UP ? t : (kChunk - 1 - t);
+        for (int t = 0; t < SH::CH; ++t) {
+          const int r = UP ? t : (SH::CH - 1 - t);
           const T tile = sm.tile[q][r][cbase];
           if (MODE == 0) uu[t] = tile;
           else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
@@ -412,8 +423,8 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
         // each y is stored one row late, so that no store waits on the FMA just issued
         T y_last = T(0);
 #pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
-          const int r = UP ? t : (kChunk - 1 - t);
+        for (int t = 0; t < SH::CH; ++t) {
+          const int r = UP ? t : (SH::CH - 1 - t);
           const T tile = sm.tile[q][r][cbase];
           if (MODE == 0) uu[t] = tile;
           else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
@@ -427,8 +438,8 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
         pend = false;
       } else {
 #pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
-          const int r = UP ? t : (kChunk - 1 - t);
+        for (int t = 0; t < SH::CH; ++t) {
+          const int r = UP ? t : (SH::CH - 1 - t);
           const T tile = sm.tile[q][r][cbase];
           if (MODE == 0) uu[t] = tile;
           else { u_prev = fma(sm.rec[q][r][cls * 8 + 0], u_prev, tile); uu[t] = u_prev; }
@@ -437,35 +448,35 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
       if (MODE != 0) {
         if (rec_chunk) {
 #pragma unroll
-          for (int t = 0; t < kChunk; ++t) {
-            const int l = UP ? l0 + t : l0 + kChunk - 1 - t;
+          for (int t = 0; t < SH::CH; ++t) {
+            const int l = UP ? l0 + t : l0 + SH::CH - 1 - t;
             const T um1 = t >= 1 ? uu[t - 1] : u_m1;
             const T um2 = t >= 2 ? uu[t - 2] : (t == 1 ? u_m1 : u_m2);
             if ((l >= rloB && l <= rhiB) || (l >= rloT && l <= rhiT))
               record_row<T, UP>(A, st, s, k, l, m, out_lane, uu[t], um1, um2, lam_rec_top, lam_rec_bot);
           }
         }
-        u_m2 = uu[kChunk - 2];
-        u_m1 = uu[kChunk - 1];
+        u_m2 = uu[SH::CH - 2];
+        u_m1 = uu[SH::CH - 1];
       }
       if (MODE == 2) {
         T* outT = A.UT + (size_t)(st.rowoff + lf) * P + col;
 #pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
+        for (int t = 0; t < SH::CH; ++t) {
           if (out_lane) *outT = uu[t];
           outT += step;
         }
       } else {
         // (B) shuffles (all issued before their first use) and the terms that do not
         //     depend on the previous row
-        T nb[kChunk];
+        T nb[SH::CH];
         if (kLateStore) {
 #pragma unroll
-          for (int t = 0; t < kChunk; ++t) nb[t] = shfl_val(uu[t], src);
+          for (int t = 0; t < SH::CH; ++t) nb[t] = shfl_val(uu[t], src);
         }
 #pragma unroll
-        for (int t = 0; t < kChunk; ++t) {
-          const int r = UP ? t : (kChunk - 1 - t);
+        for (int t = 0; t < SH::CH; ++t) {
+          const int r = UP ? t : (SH::CH - 1 - t);
           const T* rc = &sm.rec[q][r][cls * 8];
           T ncp_unused, ca, cb, chn;
           load_coef4(rc, ncp_unused, ca, cb, chn);
@@ -484,8 +495,8 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if (e == 0 ? c != 0 : c != NC - 1) continue;
-          const int te = e == 0 ? 0 : kChunk - 1;
-          const int re = UP ? te : (kChunk - 1 - te);
+          const int te = e == 0 ? 0 : SH::CH - 1;
+          const int re = UP ? te : (SH::CH - 1 - te);
           const int kind = slot_int(sm.rec[q][re][cls * 8 + 7]);
           if (kind >= 3) {
             const double lam = (kind == 3 || kind == 5) ? lam_rhs_top : lam_rhs_bot;
@@ -498,8 +509,8 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
     } else {
       if (pend) drain();
 #pragma unroll 1
-      for (int t = 0; t < kChunk; ++t) {
-        const int r = UP ? t : (kChunk - 1 - t);
+      for (int t = 0; t < SH::CH; ++t) {
+        const int r = UP ? t : (SH::CH - 1 - t);
         const int l = l0 + r;
         if (l < 0 || l >= L) continue;  // rows outside the strip (uniform)
         const T* rc = &sm.rec[q][r][cls * 8];
@@ -539,28 +550,28 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
 // One work unit: strip s, column block bx (4 warps = 120 output columns) of one
 // problem, for pass k.  Ring slots continue from chunk number cbase (so a block can
 // run several units back to back).  Returns false if a bounded wait expired.
-template <typename T, bool UP, int MODE, int FMODE, int NST>
+template <typename T, bool UP, int MODE, int FMODE, class SH>
 __device__ __forceinline__ bool pass_unit(const TmaMaps& maps, const TmaArgs<T>& X, const int k, const int s,
-                                          const int bx, TmaSmem<T, NST>& sm, const unsigned cbase) {
+                                          const int bx, TmaSmem<T, SH>& sm, const unsigned cbase) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kWarpsPerBlock) {
     if (lane != 0) return true;
     const StripInfo st = X.p.strips[s];
-    return produce_unit<T, UP, MODE, FMODE, NST>(maps, X, k, s, bx, st, sm, cbase, nullptr);
+    return produce_unit<T, UP, MODE, FMODE, SH>(maps, X, k, s, bx, st, sm, cbase, nullptr);
   }
-  return consume_unit<T, UP, MODE, FMODE, NST>(X, k, s, bx, sm, cbase, nullptr);
+  return consume_unit<T, UP, MODE, FMODE, SH>(X, k, s, bx, sm, cbase, nullptr);
 }
 
 // The dynamic shared-memory base is at least 16-byte aligned, which is what an
 // unswizzled TMA destination needs; using it directly (no integer round trip) keeps
 // every tile access a shared-memory load.
-template <typename T, bool UP, int MODE, int FMODE, int NST>
-__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+template <typename T, bool UP, int MODE, int FMODE, class SH>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, SH::MINB)
 sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const int k) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  TmaSmem<T, SH>& sm = *reinterpret_cast<TmaSmem<T, SH>*>(smem_raw);
   init_ring(sm);
-  (void)pass_unit<T, UP, MODE, FMODE, NST>(maps, X, k, blockIdx.y + X.p.strip0, blockIdx.x, sm, 0u);
+  (void)pass_unit<T, UP, MODE, FMODE, SH>(maps, X, k, blockIdx.y + X.p.strip0, blockIdx.x, sm, 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,16 +603,22 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
 // without data, so that the consumers leave as well.
 
 struct StreamUnit {
-  int inst, strip, bx, nc;  // problem, strip, column block, chunks of the strip
+  int inst, strip, bx, nc;  // problem, strip, column block, 16-row chunks of the strip (work)
   int left, right;          // list indices of the column neighbours (-1: none)
 };
 
 template <typename T>
 struct StreamProblem {
-  TmaMaps maps;    // 64-byte aligned tensor maps of this problem (global memory)
+  TmaMaps maps;    // 64-byte aligned tensor maps of this problem (global memory), 16-row boxes
+  TmaMaps maps8;   // the same with 8-row boxes
   TmaArgs<T> args;
   int nt, fmode;
 };
+
+template <class SH, typename T>
+__device__ __forceinline__ const TmaMaps& maps_for(const StreamProblem<T>& pr) {
+  return SH::CH == 8 ? pr.maps8 : pr.maps;
+}
 
 struct StreamArgs {
   const StreamUnit* units;       // sorted by decreasing nt of their problem
@@ -654,11 +671,11 @@ __device__ __forceinline__ bool wait_done(const StreamArgs& P, int a, int b, int
   }
 }
 
-template <typename T, int FMODE, int NST>
-__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+template <typename T, int FMODE, class SH>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, SH::MINB)
 sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  TmaSmem<T, SH>& sm = *reinterpret_cast<TmaSmem<T, SH>*>(smem_raw);
   init_ring(sm);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned cbase = 0;
@@ -690,19 +707,18 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
         h.inst = un.inst;
         h.strip = un.strip;
         h.bx = un.bx;
-        h.nc = un.nc;
         h.unit = u;
         h.new_args = un.inst != last_inst;
         last_inst = un.inst;
         const StreamProblem<T>& pr = probs[un.inst];
         h.st = pr.args.p.strips[un.strip];
+        h.nc = (h.st.L + SH::CH - 1) / SH::CH;
         if (j > 0) ok = wait_done(P, u, un.left, un.right, (unsigned)(j * kWarpsPerBlock));
         if (ok) {
           fence_proxy_async_global();
-          ok = (h.k & 1) ? produce_unit<T, false, 1, FMODE, NST>(pr.maps, pr.args, h.k, h.strip, h.bx, h.st, sm,
-                                                                 cbase, &h)
-                         : produce_unit<T, true, 1, FMODE, NST>(pr.maps, pr.args, h.k, h.strip, h.bx, h.st, sm,
-                                                                cbase, &h);
+          const TmaMaps& mp = maps_for<SH>(pr);
+          ok = (h.k & 1) ? produce_unit<T, false, 1, FMODE, SH>(mp, pr.args, h.k, h.strip, h.bx, h.st, sm, cbase, &h)
+                         : produce_unit<T, true, 1, FMODE, SH>(mp, pr.args, h.k, h.strip, h.bx, h.st, sm, cbase, &h);
           if (!ok) return;  // a ring wait expired; the consumers time out on their own
           cbase += (unsigned)h.nc;
           // the next ticket only now: a block that held two would sit on the second
@@ -714,8 +730,8 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
       // no more work, or a counter wait gave up: complete the next stage without
       // data (after the consumers released it) so that the consumers leave
       if (!ok) sm.abort = 1;
-      const int q = (int)(cbase % NST);
-      const unsigned use = cbase / NST;
+      const int q = (int)(cbase % SH::NST);
+      const unsigned use = cbase / SH::NST;
       if (use == 0 || mbar_wait(&sm.empty[q], (use - 1) & 1)) {
         sm.hdr[q].tail.k = -1;
         mbar_arrive(&sm.full[q]);
@@ -725,8 +741,8 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
   }
   // ------------------------------ consumers ------------------------------
   for (;;) {
-    const int q = (int)(cbase % NST);
-    if (!mbar_wait(&sm.full[q], (cbase / NST) & 1)) {
+    const int q = (int)(cbase % SH::NST);
+    if (!mbar_wait(&sm.full[q], (cbase / SH::NST) & 1)) {
       atomicExch(P.flag, 1);
       return;
     }
@@ -740,8 +756,8 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
     copy_words(&h.tail, &sm.hdr[q].tail, (int)(sizeof(StreamTail) / 4), lane, 32);
     __syncwarp();
     const int k = h.tail.k, s = h.tail.strip, bx = h.tail.bx, nc = h.tail.nc, u = h.tail.unit;
-    const bool ok = (k & 1) ? consume_unit<T, false, 1, FMODE, NST>(h.args, k, s, bx, sm, cbase, &h.tail.st)
-                            : consume_unit<T, true, 1, FMODE, NST>(h.args, k, s, bx, sm, cbase, &h.tail.st);
+    const bool ok = (k & 1) ? consume_unit<T, false, 1, FMODE, SH>(h.args, k, s, bx, sm, cbase, &h.tail.st)
+                            : consume_unit<T, true, 1, FMODE, SH>(h.args, k, s, bx, sm, cbase, &h.tail.st);
     if (!ok) return;
     // this warp's stores of the pass are visible (to loads and to TMA) before the
     // unit's counter moves
@@ -761,22 +777,23 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
 // last pass (back-substitution of step nt, u^nt stored) of every listed unit, each
 // at its own problem's nt.  Units u = blockIdx.x, blockIdx.x + gridDim.x, ...: one
 // block per unit when the grid is as large as the list, persistent blocks otherwise.
-template <typename T, int MODE, int FMODE, int NST>
-__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, 1)
+template <typename T, int MODE, int FMODE, class SH>
+__global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, SH::MINB)
 edge_pass_kernel(const StreamProblem<T>* __restrict__ probs, const StreamUnit* __restrict__ units, const int nunits) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  TmaSmem<T, NST>& sm = *reinterpret_cast<TmaSmem<T, NST>*>(smem_raw);
+  TmaSmem<T, SH>& sm = *reinterpret_cast<TmaSmem<T, SH>*>(smem_raw);
   init_ring(sm);
   unsigned cbase = 0;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const StreamUnit un = units[u];
     const StreamProblem<T>& pr = probs[un.inst];
     const int k = MODE == 0 ? 0 : pr.nt;
+    const TmaMaps& mp = maps_for<SH>(pr);
     bool ok;
-    if (MODE == 0 || !(k & 1)) ok = pass_unit<T, true, MODE, FMODE, NST>(pr.maps, pr.args, k, un.strip, un.bx, sm, cbase);
-    else ok = pass_unit<T, false, MODE, FMODE, NST>(pr.maps, pr.args, k, un.strip, un.bx, sm, cbase);
+    if (MODE == 0 || !(k & 1)) ok = pass_unit<T, true, MODE, FMODE, SH>(mp, pr.args, k, un.strip, un.bx, sm, cbase);
+    else ok = pass_unit<T, false, MODE, FMODE, SH>(mp, pr.args, k, un.strip, un.bx, sm, cbase);
     if (!ok) return;
-    cbase += (unsigned)un.nc;
+    cbase += (unsigned)((pr.args.p.strips[un.strip].L + SH::CH - 1) / SH::CH);
   }
 }
 

@@ -9,7 +9,9 @@
 // either as direct launches or as one replayed CUDA graph.
 #include "../../include/kfp_swr.h"
 #include "kfp_kernels.cuh"
+#include "kfp_reduce.cuh"
 #include "kfp_sweep_tma.cuh"
+#include "kfp_launch.h"
 #include "kfp_adjoint.cuh"
 #include "kfp_fe.cuh"
 
@@ -28,6 +30,49 @@
 namespace {
 
 thread_local std::string g_create_error;
+
+// Runtime choice of the tile shape of the TMA-fed sweep (kfp_launch.h).
+template <typename T>
+struct Tma {
+  static size_t smem_bytes(int sh) {
+    return sh == 0 ? kfp::LaunchSet<T, 0>::smem_bytes()
+                   : (sh == 1 ? kfp::LaunchSet<T, 1>::smem_bytes() : kfp::LaunchSet<T, 2>::smem_bytes());
+  }
+  static cudaError_t set_attrs() {
+    cudaError_t e = kfp::LaunchSet<T, 0>::set_attrs();
+    if (e == cudaSuccess) e = kfp::LaunchSet<T, 1>::set_attrs();
+    if (e == cudaSuccess) e = kfp::LaunchSet<T, 2>::set_attrs();
+    return e;
+  }
+  static int blocks_per_sm(int sh, int fmode) {
+    return sh == 0 ? kfp::LaunchSet<T, 0>::blocks_per_sm(fmode)
+                   : (sh == 1 ? kfp::LaunchSet<T, 1>::blocks_per_sm(fmode) : kfp::LaunchSet<T, 2>::blocks_per_sm(fmode));
+  }
+  static void pass(int sh, int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const kfp::TmaMaps& maps,
+                   const kfp::TmaArgs<T>& X, int k) {
+    if (sh == 0) kfp::LaunchSet<T, 0>::pass(fmode, up, mode, grid, st, maps, X, k);
+    else if (sh == 1) kfp::LaunchSet<T, 1>::pass(fmode, up, mode, grid, st, maps, X, k);
+    else kfp::LaunchSet<T, 2>::pass(fmode, up, mode, grid, st, maps, X, k);
+  }
+  static cudaError_t stream(int sh, int fmode, unsigned grid, cudaStream_t st, const kfp::StreamProblem<T>* probs,
+                            const kfp::StreamArgs& P) {
+    if (sh == 0) return kfp::LaunchSet<T, 0>::stream(fmode, grid, st, probs, P);
+    if (sh == 1) return kfp::LaunchSet<T, 1>::stream(fmode, grid, st, probs, P);
+    return kfp::LaunchSet<T, 2>::stream(fmode, grid, st, probs, P);
+  }
+  static void edge(int sh, int mode, int fmode, unsigned grid, cudaStream_t st, const kfp::StreamProblem<T>* probs,
+                   const kfp::StreamUnit* units, int n) {
+    if (sh == 0) kfp::LaunchSet<T, 0>::edge(mode, fmode, grid, st, probs, units, n);
+    else if (sh == 1) kfp::LaunchSet<T, 1>::edge(mode, fmode, grid, st, probs, units, n);
+    else kfp::LaunchSet<T, 2>::edge(mode, fmode, grid, st, probs, units, n);
+  }
+};
+
+// Tile shape requested through the descriptor flags (-1: choose automatically).
+int requested_shape(unsigned flags) {
+  const int f = (int)((flags >> KFP_FLAG_SHAPE_SHIFT) & 3u);
+  return f == 0 ? -1 : f - 1;
+}
 
 // Return a status with the CUDA error text; OBJ is the handle whose message is set.
 #define KFP_CUDA_TRY_ON(OBJ, call)                                                        \
@@ -253,6 +298,8 @@ struct kfp_swr {
   // persistent (streamed) sweep: the interior passes of an iteration in one co-resident
   // launch (one per strip in the serial form)
   int persist = 0, persist_grid = 0, nbx = 0;
+  int shape = 0;               // tile shape of the TMA-fed sweep (kfp_launch.h)
+  kfp::TmaMaps maps8;          // tensor maps with 8-row boxes (shapes 1 and 2)
   unsigned* done = nullptr;    // [S * nbx] per-unit completion counters, then [S] tickets
   void* sprob = nullptr;       // device StreamProblem<T> of this handle
   kfp::StreamUnit* sunits = nullptr;  // [S * nbx], strip-major
@@ -364,9 +411,7 @@ struct kfp_swr {
   template <typename T>
   void enqueue_passes(cudaStream_t st) const {
     if (use_tma) {
-      if (fmode == 0) enqueue_passes_tma<T, 0>(st);
-      else if (fmode == 1) enqueue_passes_tma<T, 1>(st);
-      else enqueue_passes_tma<T, 2>(st);
+      enqueue_passes_tma<T>(st);
       return;
     }
     kfp::PassArgs<T> A = pass_args<T>();
@@ -434,39 +479,32 @@ struct kfp_swr {
     return E;
   }
 
-  template <typename T>
-  static constexpr int tma_stages() { return sizeof(T) == 8 ? 4 : 8; }
-  template <typename T>
-  static size_t tma_smem_bytes() { return sizeof(kfp::TmaSmem<T, tma_stages<T>()>) + 128; }
+  // Tensor maps with the box height of this handle's tile shape.
+  const kfp::TmaMaps& shape_maps() const { return kfp::shape_rows(shape) == 8 ? maps8 : maps; }
 
   // The persistent sweep, per group of strips (all strips; one strip at a time in the
   // serial form): the first pass, the nt-1 interior passes in one cooperative launch
   // of the streamed kernel (after the units' counters and tickets are zeroed), the
   // last pass.
-  template <typename T, int FM>
+  template <typename T>
   void enqueue_persistent(cudaStream_t st, bool interior_only = false) const {
-    constexpr int NST = tma_stages<T>();
     kfp::TmaArgs<T> X = tma_args<T>();
     const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
     const int groups = serial ? g.S : 1;
-    const dim3 pgrid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
-    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
-    const size_t smem = tma_smem_bytes<T>();
+    const dim3 pgrid(nbx_tma(), serial ? 1 : g.S);
     if (g.nt > 1) cudaMemsetAsync(done, 0, sizeof(unsigned) * ((size_t)g.S * nbx + g.S), st);
     for (int grp = 0; grp < groups; ++grp) {
       X.p.strip0 = serial ? grp : 0;
-      if (!interior_only) kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<pgrid, block, smem, st>>>(maps, X, 0);
-      if (g.nt > 1) enqueue_interior<T, FM>(st, serial ? grp : -1);
+      if (!interior_only) Tma<T>::pass(shape, fmode, true, 0, pgrid, st, shape_maps(), X, 0);
+      if (g.nt > 1) enqueue_interior<T>(st, serial ? grp : -1);
       if (interior_only) continue;
-      if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
-      else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<pgrid, block, smem, st>>>(maps, X, g.nt);
+      Tma<T>::pass(shape, fmode, !(g.nt & 1), 2, pgrid, st, shape_maps(), X, g.nt);
     }
   }
 
   // Interior passes of all strips (strip < 0) or of one strip (serial form).
-  template <typename T, int FM>
+  template <typename T>
   void enqueue_interior(cudaStream_t st, int strip) const {
-    constexpr int NST = tma_stages<T>();
     const int base = strip < 0 ? 0 : strip * nbx;
     kfp::StreamArgs P;
     P.units = sunits + base;
@@ -478,76 +516,43 @@ struct kfp_swr {
     P.flag = flag;
     P.stall_unit = stall_unit;
     P.wait_ns = wait_ns;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)persist_grid);
-    cfg.blockDim = dim3((kfp::kWarpsPerBlock + 1) * 32);
-    cfg.dynamicSmemBytes = tma_smem_bytes<T>();
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kfp::sweep_stream_kernel<T, FM, NST>, (const kfp::StreamProblem<T>*)sprob, P);
+    Tma<T>::stream(shape, fmode, (unsigned)persist_grid, st, (const kfp::StreamProblem<T>*)sprob, P);
   }
 
-  template <typename T, int FM>
+  template <typename T>
   void enqueue_passes_tma(cudaStream_t st) const {
     if (persist) {
-      enqueue_persistent<T, FM>(st);
+      enqueue_persistent<T>(st);
       return;
     }
-    constexpr int NST = tma_stages<T>();
     kfp::TmaArgs<T> X = tma_args<T>();
     const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
     const int groups = serial ? g.S : 1;
-    const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, serial ? 1 : g.S);
-    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
-    const size_t sm = tma_smem_bytes<T>();
+    const dim3 grid(nbx_tma(), serial ? 1 : g.S);
+    const kfp::TmaMaps& mp = shape_maps();
     for (int grp = 0; grp < groups; ++grp) {
       X.p.strip0 = serial ? grp : 0;
-      kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST><<<grid, block, sm, st>>>(maps, X, 0);
+      // pass k runs in ascending row order when k is even (step 1 is factored upward)
+      Tma<T>::pass(shape, fmode, true, 0, grid, st, mp, X, 0);
       wrap_after_pass<T>(st, 0, X.p.strip0, serial ? 1 : g.S);
       for (int k = 1; k < g.nt; ++k) {
-        if (k & 1) kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
-        else       kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST><<<grid, block, sm, st>>>(maps, X, k);
+        Tma<T>::pass(shape, fmode, !(k & 1), 1, grid, st, mp, X, k);
         wrap_after_pass<T>(st, k, X.p.strip0, serial ? 1 : g.S);
       }
-      if (g.nt & 1) kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
-      else          kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST><<<grid, block, sm, st>>>(maps, X, g.nt);
+      Tma<T>::pass(shape, fmode, !(g.nt & 1), 2, grid, st, mp, X, g.nt);
     }
   }
 
-  template <typename T, int FM>
-  cudaError_t set_tma_smem_attr() const {
-    constexpr int NST = tma_stages<T>();
-    const int sm = (int)tma_smem_bytes<T>();
-    cudaError_t e = cudaSuccess;
-    auto set = [&](const void* fn) {
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    };
-    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 0, FM, NST>);
-    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 1, FM, NST>);
-    set((const void*)kfp::sweep_pass_tma_kernel<T, false, 1, FM, NST>);
-    set((const void*)kfp::sweep_pass_tma_kernel<T, true, 2, FM, NST>);
-    set((const void*)kfp::sweep_pass_tma_kernel<T, false, 2, FM, NST>);
-    set((const void*)kfp::sweep_stream_kernel<T, FM, NST>);
-    return e;
-  }
-
-  // Blocks of the streamed sweep that fit on the device at once (0 if none).
-  template <typename T, int FM>
+  // Blocks of the streamed sweep in this handle's shape that fit on the device at
+  // once (0 if none).
+  template <typename T>
   int persistent_capacity() const {
-    constexpr int NST = tma_stages<T>();
-    int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_stream_kernel<T, FM, NST>,
-                                                      (kfp::kWarpsPerBlock + 1) * 32, tma_smem_bytes<T>()) !=
-            cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    return per_sm * sms;
+    return Tma<T>::blocks_per_sm(shape, fmode) * sms;
   }
 
   void record(int idx, cudaStream_t st, bool capturing) const {
@@ -1032,27 +1037,35 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
   rc = alloc(h, (void**)&h->flag, sizeof(int));
   if (rc) return rc;
   KFP_CUDA_TRY_H(cudaMemset(h->flag, 0, sizeof(int)));
-  // tensor maps
-  rc = encode_2d(h, &h->maps.state, h->Ybuf, (size_t)2 * g.rows, g.P, kfp::kChunk, kfp::kBoxW);
-  if (!rc) rc = encode_2d(h, &h->maps.init, h->U0, g.nv + 1, g.P, kfp::kChunk, kfp::kBoxW);
-  if (!rc && h->fmode == 1) rc = encode_2d(h, &h->maps.force, h->GF, (size_t)2 * g.rows, g.P, kfp::kChunk, kfp::kBoxW);
-  if (!rc && h->fmode == 2) rc = encode_2d(h, &h->maps.force, h->F, g.nv + 1, g.P, kfp::kChunk, kfp::kBoxW);
-  if (!rc && h->fmode == 0) h->maps.force = h->maps.init;  // never read
-  if (!rc) rc = encode_2d(h, &h->maps.rec, h->rec, (size_t)g.S * 2 * h->Lpad, kfp::kRecW, kfp::kChunk, kfp::kRecW);
-  if (rc) return rc;
-  cudaError_t e = h->fmode == 0 ? h->set_tma_smem_attr<T, 0>()
-                                : (h->fmode == 1 ? h->set_tma_smem_attr<T, 1>() : h->set_tma_smem_attr<T, 2>());
+  // tensor maps, with 16-row and 8-row boxes (the rows of a ring stage of each shape)
+  for (int box : {16, 8}) {
+    kfp::TmaMaps& m = box == 16 ? h->maps : h->maps8;
+    rc = encode_2d(h, &m.state, h->Ybuf, (size_t)2 * g.rows, g.P, box, kfp::kBoxW);
+    if (!rc) rc = encode_2d(h, &m.init, h->U0, g.nv + 1, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 1) rc = encode_2d(h, &m.force, h->GF, (size_t)2 * g.rows, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 2) rc = encode_2d(h, &m.force, h->F, g.nv + 1, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 0) m.force = m.init;  // never read
+    if (!rc) rc = encode_2d(h, &m.rec, h->rec, (size_t)g.S * 2 * h->Lpad, kfp::kRecW, box, kfp::kRecW);
+    if (rc) return rc;
+  }
+  cudaError_t e = Tma<T>::set_attrs();
   if (e != cudaSuccess) return h->fail(KFP_ECUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
   h->use_tma = 1;
+  // Tile shape: 16-row stages and one block per SM when a pass has at most one unit
+  // per SM, otherwise 8-row stages and two blocks per SM (two consumer warps per
+  // sub-partition hide each other's latencies) -- unless the flags fix one.
   // Streamed sweep when forced, or by default when a pass has more units than the
   // device holds blocks at once (then it beats one launch per pass; below that the
   // neighbour wait costs more than the launch it saves).  Periodic x needs its
   // column wrap between passes and keeps one launch per pass.
   KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
-  const int cap = h->fmode == 0 ? h->persistent_capacity<T, 0>()
-                                : (h->fmode == 1 ? h->persistent_capacity<T, 1>() : h->persistent_capacity<T, 2>());
+  int sms = 0;
+  KFP_CUDA_TRY_H(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const bool serial = (h->flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
   const int units_per_pass = (serial ? 1 : g.S) * h->nbx_tma();
+  h->shape = requested_shape(h->flags);
+  if (h->shape < 0) h->shape = units_per_pass > sms ? 1 : 0;
+  const int cap = h->persistent_capacity<T>();
   const bool want = (h->flags & KFP_FLAG_PERSISTENT) ||
                     (!(h->flags & KFP_FLAG_PER_PASS) && g.nt > 2 && units_per_pass > cap);
   if (want && !g.periodic) {
@@ -1076,7 +1089,7 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
           un.inst = 0;
           un.strip = s;
           un.bx = bx;
-          un.nc = (g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk;
+          un.nc = (g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax;
           un.left = bx > 0 ? rel - 1 : -1;
           un.right = bx + 1 < nbx ? rel + 1 : -1;
         }
@@ -1099,6 +1112,7 @@ kfp_status upload_stream_problem(kfp_swr* h) {
   kfp::StreamProblem<T> sp;
   std::memset(&sp, 0, sizeof sp);
   sp.maps = h->maps;
+  sp.maps8 = h->maps8;
   sp.args = h->tma_args<T>();
   sp.nt = h->g.nt;
   sp.fmode = h->fmode;
@@ -1508,6 +1522,7 @@ struct kfp_batch {
   int grp_pass_off[3] = {0, 0, 0};       // group f's pass table in pass_dev
   int max_nt = 0, sms = 1, stream_grid = 0;
   int blocks_per_sm = 0;               // first/last passes: 0 = one block per unit; > 0 persistent grid
+  int shape = 1;                       // tile shape of the streamed interior passes (kfp_launch.h)
   int unit_order = 0;                  // within a pass: 0 = taller strips first; 1 = problem order
   int* flag = nullptr;                 // error flag of the streamed launches
   long long iterations = 0, cells_per_iter = 0;
@@ -1529,8 +1544,6 @@ struct kfp_batch {
     return c;
   }
 
-  template <typename T>
-  static constexpr int nst() { return kfp_swr::tma_stages<T>(); }
 
   // List the units: by forcing mode (one streamed launch per mode), then by
   // decreasing nt (the units of interior pass k are then a prefix of the group),
@@ -1586,60 +1599,55 @@ struct kfp_batch {
     return all;
   }
 
-  template <typename T, int FM>
-  void enqueue_group(cudaStream_t st, int mode) const {
-    constexpr int NST = nst<T>();
-    const size_t sm = kfp_swr::tma_smem_bytes<T>();
+  // First pass (mode 0) or streamed interior passes (mode 1) of forcing-mode group fm.
+  template <typename T>
+  void enqueue_group(cudaStream_t st, int fm, int mode) const {
     const auto* probs = (const kfp::StreamProblem<T>*)probs_dev;
-    const int n = grp_begin[FM + 1] - grp_begin[FM];
+    const int n = grp_begin[fm + 1] - grp_begin[fm];
     if (n == 0) return;
-    const dim3 block((kfp::kWarpsPerBlock + 1) * 32);
     if (mode == 0) {
       const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
-      kfp::edge_pass_kernel<T, 0, FM, NST><<<grid, block, sm, st>>>(probs, units_dev + grp_begin[FM], n);
+      Tma<T>::edge(0, 0, fm, (unsigned)grid, st, probs, units_dev + grp_begin[fm], n);
       return;
     }
-    if (grp_npass[FM] == 0) return;
+    if (grp_npass[fm] == 0) return;
     kfp::StreamArgs P;
-    P.units = units_dev + grp_begin[FM];
-    P.pass_start = pass_dev + grp_pass_off[FM];
-    P.npass = grp_npass[FM];
+    P.units = units_dev + grp_begin[fm];
+    P.pass_start = pass_dev + grp_pass_off[fm];
+    P.npass = grp_npass[fm];
     P.dynamic = n > stream_grid ? 1 : 0;  // the first pass is the largest
-    P.done = done + grp_begin[FM];
-    P.ticket = done + units.size() + FM;
+    P.done = done + grp_begin[fm];
+    P.ticket = done + units.size() + fm;
     P.flag = flag;
     P.stall_unit = -1;
     P.wait_ns = 4000000000ull;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)stream_grid);
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = sm;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kfp::sweep_stream_kernel<T, FM, NST>, probs, P);
+    Tma<T>::stream(shape, fm, (unsigned)stream_grid, st, probs, P);
   }
 
   // One iteration's passes: the first pass of every unit, the interior passes in one
-  // streamed launch per forcing mode, the last pass of every unit.
+  // streamed launch per forcing mode, the last pass of every unit.  The first and
+  // last passes use 16-row stages; the interior passes the configured shape.
   template <typename T>
   void enqueue_passes(cudaStream_t st) const {
-    constexpr int NST = nst<T>();
-    const size_t sm = kfp_swr::tma_smem_bytes<T>();
     cudaMemsetAsync(done, 0, sizeof(unsigned) * (units.size() + 3), st);
-    enqueue_group<T, 0>(st, 0);
-    enqueue_group<T, 1>(st, 0);
-    enqueue_group<T, 2>(st, 0);
-    enqueue_group<T, 0>(st, 1);
-    enqueue_group<T, 1>(st, 1);
-    enqueue_group<T, 2>(st, 1);
+    for (int fm = 0; fm < 3; ++fm) enqueue_group<T>(st, fm, 0);
+    for (int fm = 0; fm < 3; ++fm) enqueue_group<T>(st, fm, 1);
     const int n = (int)units.size();
     const int grid = blocks_per_sm > 0 ? std::min(n, blocks_per_sm * sms) : n;
-    kfp::edge_pass_kernel<T, 2, 0, NST><<<grid, (kfp::kWarpsPerBlock + 1) * 32, sm, st>>>(
-        (const kfp::StreamProblem<T>*)probs_dev, units_dev, n);
+    Tma<T>::edge(0, 2, 0, (unsigned)grid, st, (const kfp::StreamProblem<T>*)probs_dev, units_dev, n);
+  }
+
+  // Blocks of the streamed kernel of the configured shape resident at once.
+  template <typename T>
+  int stream_capacity() const {
+    int per_sm = 0;
+    for (int fm = 0; fm < 3; ++fm)
+      if (grp_begin[fm + 1] > grp_begin[fm]) {
+        const int b = Tma<T>::blocks_per_sm(shape, fm);
+        per_sm = per_sm == 0 ? b : std::min(per_sm, b);
+      }
+    if (per_sm == 0) per_sm = Tma<T>::blocks_per_sm(shape, 1);
+    return per_sm * sms;
   }
 
   void enqueue_iteration(cudaStream_t st, bool capturing) const {
@@ -1666,6 +1674,8 @@ struct kfp_batch {
   kfp_status upload_units() {
     order_units();
     const std::vector<int> tables = pass_tables();
+    stream_grid = prec == KFP_F64 ? stream_capacity<double>() : stream_capacity<float>();
+    if (stream_grid < 1) return fail(KFP_ECUDA, "the streamed sweep does not fit on an SM in shape %d", shape);
     if (units_dev) cudaFree(units_dev);
     if (pass_dev) cudaFree(pass_dev);
     units_dev = nullptr;
@@ -1783,6 +1793,7 @@ kfp_status batch_setup(kfp_batch* b) {
     kfp_swr* h = b->inst[i];
     std::memset(&host[i], 0, sizeof host[i]);
     host[i].maps = h->maps;
+    host[i].maps8 = h->maps8;
     host[i].args = h->tma_args<T>();
     host[i].nt = h->g.nt;
     host[i].fmode = h->fmode;
@@ -1791,7 +1802,7 @@ kfp_status batch_setup(kfp_batch* b) {
     const int nbx = h->nbx_tma();
     for (int s = 0; s < h->g.S; ++s)
       for (int bx = 0; bx < nbx; ++bx)
-        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunk - 1) / kfp::kChunk, -1, -1});
+        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax, -1, -1});
   }
   KFP_CUDA_TRY_ON(b, cudaMalloc(&b->probs_dev, sizeof(kfp::StreamProblem<T>) * host.size()));
   KFP_CUDA_TRY_ON(b, cudaMemcpy(b->probs_dev, host.data(), sizeof(kfp::StreamProblem<T>) * host.size(),
@@ -1799,21 +1810,8 @@ kfp_status batch_setup(kfp_batch* b) {
   KFP_CUDA_TRY_ON(b, cudaMalloc(&b->done, sizeof(unsigned) * (b->units.size() + 3)));
   KFP_CUDA_TRY_ON(b, cudaMalloc(&b->flag, sizeof(int)));
   KFP_CUDA_TRY_ON(b, cudaMemset(b->flag, 0, sizeof(int)));
-  constexpr int NST = kfp_batch::nst<T>();
-  const int sm = (int)kfp_swr::tma_smem_bytes<T>();
-  auto attr = [&](const void* fn) { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); };
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 0, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 1, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 0, 2, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::edge_pass_kernel<T, 2, 0, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 0, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 1, NST>));
-  KFP_CUDA_TRY_ON(b, attr((const void*)kfp::sweep_stream_kernel<T, 2, NST>));
-  int per_sm = 0;
-  KFP_CUDA_TRY_ON(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfp::sweep_stream_kernel<T, 1, NST>,
-                                                                  (kfp::kWarpsPerBlock + 1) * 32, sm));
-  if (per_sm < 1) return b->fail(KFP_ECUDA, "the streamed sweep does not fit on an SM");
-  b->stream_grid = per_sm * b->sms;
+  KFP_CUDA_TRY_ON(b, Tma<T>::set_attrs());
+  b->stream_grid = 0;
   return b->upload_units();
 }
 
@@ -2054,12 +2052,15 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
   return KFP_OK;
 }
 
-kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order) {
+kfp_status kfp_batch_configure(kfp_batch_t b, int blocks_per_sm, int unit_order, int tile_shape) {
   if (!b) return KFP_EINVAL;
-  if (blocks_per_sm < 0 || blocks_per_sm > 64 || unit_order < 0 || unit_order > 1)
-    return b->fail(KFP_EINVAL, "need 0 <= blocks_per_sm <= 64 and unit_order in {0, 1}");
+  if (blocks_per_sm < 0 || blocks_per_sm > 64 || unit_order < 0 || unit_order > 1 || tile_shape < 0 ||
+      tile_shape >= kfp::kShapes)
+    return b->fail(KFP_EINVAL, "need 0 <= blocks_per_sm <= 64, unit_order in {0, 1} and tile_shape in 0..%d",
+                   kfp::kShapes - 1);
   b->blocks_per_sm = blocks_per_sm;
   b->unit_order = unit_order;
+  b->shape = tile_shape;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return b->fail(KFP_ECUDA, "sync failed");
   return b->upload_units();
 }
@@ -2136,15 +2137,8 @@ extern "C" kfp_status kfp_swr_selftest_stall(kfp_swr_t h, int unit, double limit
   h->stall_unit = unit;
   h->wait_ns = (unsigned long long)(limit_s * 1e9);
   // the interior sweep passes only: the interface data and the norms stay as they are
-  if (h->prec == KFP_F64) {
-    if (h->fmode == 0) h->enqueue_persistent<double, 0>(h->stream, true);
-    else if (h->fmode == 1) h->enqueue_persistent<double, 1>(h->stream, true);
-    else h->enqueue_persistent<double, 2>(h->stream, true);
-  } else {
-    if (h->fmode == 0) h->enqueue_persistent<float, 0>(h->stream, true);
-    else if (h->fmode == 1) h->enqueue_persistent<float, 1>(h->stream, true);
-    else h->enqueue_persistent<float, 2>(h->stream, true);
-  }
+  if (h->prec == KFP_F64) h->enqueue_persistent<double>(h->stream, true);
+  else h->enqueue_persistent<float>(h->stream, true);
   h->stall_unit = -1;
   h->wait_ns = keep;
   KFP_CUDA_TRY_ON(h, cudaGetLastError());

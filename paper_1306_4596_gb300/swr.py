@@ -26,6 +26,13 @@ PRECISIONS = {"f64": KFP_F64, "f32": KFP_F32, "mixed": KFP_MIXED}
 KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1, 2, 4, 8
 KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME, KFP_FLAG_PERSISTENT = 16, 32, 64, 128
 KFP_FLAG_PER_PASS = 256
+KFP_FLAG_SHAPE_SHIFT = 9
+TILE_SHAPES = 3
+
+
+def KFP_FLAG_SHAPE(n: int) -> int:
+    """Flag fixing the tile shape n (0..2) of the TMA-fed sweep."""
+    return (n + 1) << KFP_FLAG_SHAPE_SHIFT
 
 
 def problem_flags(prob) -> int:
@@ -99,7 +106,7 @@ def load(rebuild: bool = False):
             lib.kfp_swr_counters.restype = ctypes.c_int
             lib.kfp_batch_create.argtypes = [ctypes.POINTER(kfp_swr_desc), ctypes.POINTER(kfp_swr_problem), i, vp,
                                              ctypes.POINTER(vp)]
-            lib.kfp_batch_configure.argtypes = [vp, i, i]
+            lib.kfp_batch_configure.argtypes = [vp, i, i, i]
             lib.kfp_batch_sweep.argtypes = [vp, i, ctypes.c_double, i, ip]
             lib.kfp_batch_instance.argtypes = [vp, i, ctypes.POINTER(vp)]
             lib.kfp_batch_stats.argtypes = [vp, llp, llp, _dp, _dp]
@@ -331,8 +338,8 @@ class Batch:
             raise KfpError(st, load().kfp_batch_last_error(self.b).decode())
         return st
 
-    def configure(self, blocks_per_sm: int = 0, unit_order: int = 0) -> None:
-        self._check(load().kfp_batch_configure(self.b, blocks_per_sm, unit_order))
+    def configure(self, blocks_per_sm: int = 0, unit_order: int = 0, tile_shape: int = 1) -> None:
+        self._check(load().kfp_batch_configure(self.b, blocks_per_sm, unit_order, tile_shape))
 
     def sweep(self, max_iters: int, tol: float = 0.0, tol_kind: int = 0, allow_notconv: bool = True) -> int:
         done = ctypes.c_int()
@@ -389,7 +396,8 @@ class SWR:
     handed over and the library copies them in."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
-                 graph: bool = True, profile: bool = False, generic: bool = False, persistent: Optional[bool] = None):
+                 graph: bool = True, profile: bool = False, generic: bool = False, persistent: Optional[bool] = None,
+                 tile_shape: Optional[int] = None):
         import torch
 
         self.prob = prob
@@ -417,6 +425,7 @@ class SWR:
         flags = ((0 if graph else KFP_FLAG_NO_GRAPH) | (KFP_FLAG_PROFILE if profile else 0)
                  | (KFP_FLAG_GENERIC if generic else 0)
                  | {None: 0, True: KFP_FLAG_PERSISTENT, False: KFP_FLAG_PER_PASS}[persistent]
+                 | (0 if tile_shape is None else KFP_FLAG_SHAPE(tile_shape))
                  | problem_flags(prob))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,

@@ -1,4 +1,5 @@
-"""Batched sweep: many uneven problems in one launch per time step.
+"""Batched sweep: many uneven problems swept together (first pass, streamed interior
+passes, last pass per iteration).
 
 Every problem of a batch runs exactly the arithmetic of its own handle, so its
 results must be bit-identical to a single-problem run, for every launch shape the
@@ -41,31 +42,38 @@ def test_batch_equals_single_problem_runs(precision):
     probs = batch_problems()
     iters = 3
     ref = [single_results(p, precision, iters) for p in probs]
-    for bps, order in ((0, 0), (1, 0), (1, 1), (2, 1)):
+    for bps, order, shape in ((0, 0, 1), (1, 0, 0), (1, 1, 2), (2, 1, 1), (0, 1, 0)):
         with swr.Batch(probs, precision) as b:
-            b.configure(bps, order)
+            b.configure(bps, order, shape)
             n = b.sweep(iters)
             assert n == iters
             for i, p in enumerate(probs):
                 v = b.view(i)
                 u, lam, hist = v.solution(), v.traces(), v.error()[3]
-                assert np.array_equal(u, ref[i][0]), (bps, order, i)
-                assert np.array_equal(lam, ref[i][1]), (bps, order, i)
-                assert np.array_equal(hist, ref[i][2]), (bps, order, i)
+                assert np.array_equal(u, ref[i][0]), (bps, order, shape, i)
+                assert np.array_equal(lam, ref[i][1]), (bps, order, shape, i)
+                assert np.array_equal(hist, ref[i][2]), (bps, order, shape, i)
 
 
+# strip heights - 1 (nv / S) whose chunk count equals the ring depth of each tile
+# shape: shape 0 has 16-row stages (4 FP64 / 8 FP32 of them), shape 1 8-row stages
+# (4 / 8), shape 2 8-row stages (6 / 12)
+RING_ROWS = {(0, "f64"): 60, (0, "f32"): 120, (1, "f64"): 30, (1, "f32"): 60, (2, "f64"): 46, (2, "f32"): 94}
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_batch_units_as_long_as_the_ring(precision):
-    """Problems whose strips take exactly as many chunks as the ring has stages (4 in
-    FP64, 8 in FP32; 16 rows per chunk), so that a unit's successor starts in the
-    stage of the unit's own first chunk while that unit is still running, with
-    different problems (other arrays) back to back."""
+def test_batch_units_as_long_as_the_ring(precision, shape):
+    """Problems whose strips take exactly as many chunks as the ring has stages, so
+    that a unit's successor starts in the stage of the unit's own first chunk while
+    that unit is still running, with different problems (other arrays) back to back."""
     from paper_1306_4596_gb300 import swr
-    rows = 60 if precision == "f64" else 120  # nv / S: strips of 61 or 121 rows, 4 or 8 chunks
+    rows = RING_ROWS[(shape, precision)]
     probs = [RD(90 + 7 * i, rows * S, 5 + i, 0.002, S, 0, True, p=3.0 + i, seed=90 + i, nforce=1,
                 boundary_data=False) for i, S in enumerate((2, 3, 4, 2, 3))]
     ref = [single_results(p, precision, 2) for p in probs]
     with swr.Batch(probs, precision) as b:
+        b.configure(0, 1, shape)
         b.sweep(2)
         for i in range(len(probs)):
             v = b.view(i)
@@ -95,14 +103,15 @@ def test_batch_tolerance_and_autotune(tmp_path, monkeypatch):
              inputs.gaussian_bumps(96, 128, 30, 2.5e-3, 4, p=6.0, seed=7)]
     with swr.Batch(probs, "f64") as b:
         t1 = autotune.tune(b, "f64")
-        assert not t1["cached"] and len(t1["candidates"]) == 4
+        assert not t1["cached"] and len(t1["candidates"]) == len(autotune.CANDIDATES) >= 8
         n = b.sweep(300, 1e-12, 1)
         assert n < 300
         for i in range(2):
             assert b.view(i).error()[0] < 1e-12
     with swr.Batch(probs, "f64") as b:
         t2 = autotune.tune(b, "f64")
-        assert t2["cached"] and (t2["blocks_per_sm"], t2["unit_order"]) == (t1["blocks_per_sm"], t1["unit_order"])
+        assert t2["cached"] and (t2["blocks_per_sm"], t2["unit_order"], t2["tile_shape"]) == (
+            t1["blocks_per_sm"], t1["unit_order"], t1["tile_shape"])
 
 
 def test_batch_rejects_unsupported():

@@ -108,3 +108,17 @@ def test_stall_check_needs_the_persistent_sweep():
     from paper_1306_4596_gb300 import swr
     with swr.SWR(inputs.small_robin()) as s:
         assert swr.kfp_swr_selftest_stall(s.h, 0, 0.05) == swr.KFP_ENOTSUP
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,iters", [CASES[4], CASES[5], CASES[7]], ids=[CASES[4][0], CASES[5][0],
+                                                                                    CASES[7][0]])
+def test_tile_shapes_are_bitwise_identical(label, factory, iters, precision):
+    """Every tile shape (16- or 8-row ring stages, one or two blocks per SM), in the
+    per-pass and in the streamed form, gives the same bits."""
+    prob = factory()
+    ref = _run(prob, iters, precision, persistent=False, tile_shape=0)
+    for shape in (0, 1, 2):
+        for persistent in (False, True):
+            if (shape, persistent) != (0, False):
+                _same(ref, _run(prob, iters, precision, persistent=persistent, tile_shape=shape))

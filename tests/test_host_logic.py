@@ -17,8 +17,8 @@ class _FakeBatch:
         self.probs = probs
         self.configured = []
 
-    def configure(self, bps, order):
-        self.configured.append((bps, order))
+    def configure(self, bps, order, shape=1):
+        self.configured.append((bps, order, shape))
 
 
 def test_autotune_signature_ignores_problem_order_but_not_precision():
@@ -33,11 +33,16 @@ def test_autotune_applies_a_cached_choice_without_timing(tmp_path, monkeypatch):
     monkeypatch.setenv("KFP_SWR_CACHE", str(tmp_path))
     probs = inputs.batch_instances(3)
     key = autotune.signature(probs, "f64")
-    entry = {"blocks_per_sm": 1, "unit_order": 0, "ms": 1.5, "candidates": []}
+    entry = {"blocks_per_sm": 1, "unit_order": 0, "tile_shape": 2, "ms": 1.5, "candidates": []}
     (tmp_path / "autotune.json").write_text(json.dumps({key: entry}))
     fake = _FakeBatch(probs)
     res = autotune.tune(fake, "f64")
-    assert res["cached"] and fake.configured == [(1, 0)]
+    assert res["cached"] and fake.configured == [(1, 0, 2)]
+
+
+def test_autotune_candidates_cover_every_tile_shape():
+    assert len(autotune.CANDIDATES) >= 8 and len(set(autotune.CANDIDATES)) == len(autotune.CANDIDATES)
+    assert {c[2] for c in autotune.CANDIDATES} == set(range(swr.TILE_SHAPES))
 
 
 def test_table1_formatting():
