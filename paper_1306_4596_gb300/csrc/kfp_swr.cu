@@ -17,6 +17,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -30,6 +31,16 @@
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range for the host timeline of a profiler (kfp.iteration, kfp.sweep,
+// kfp.exchange, kfp.error): it marks where the host enqueues (or captures) the
+// work; device times come from CUDA events or the profiler's kernel list.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Runtime choice of the tile shape of the TMA-fed sweep (kfp_launch.h).
 template <typename T>
@@ -570,10 +581,14 @@ struct kfp_swr {
 
   void enqueue_iteration(cudaStream_t st, bool capturing, int kind) const {
     record(0, st, capturing);
-    if (prec == KFP_F64) enqueue_passes<double>(st);
-    else enqueue_passes<float>(st);
+    {
+      NvtxRange r("kfp.sweep");
+      if (prec == KFP_F64) enqueue_passes<double>(st);
+      else enqueue_passes<float>(st);
+    }
     record(1, st, capturing);
     if (g.S > 1) {
+      NvtxRange r("kfp.exchange");
       if (kind == kStandard)
         kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
             lam_next, lam_in, n_trace, partial, tickets + 0, scal);
@@ -586,6 +601,7 @@ struct kfp_swr {
     }
     record(2, st, capturing);
     if (g.S > 1 && kind != kInner) {
+      NvtxRange r("kfp.error");
       kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
           bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
           scal, hist, iter, hist_cap, g.periodic ? g.nx + 1 : 0);
@@ -655,6 +671,7 @@ struct kfp_swr {
   // Launch one iteration of the given kind (graph replay or direct launches) and,
   // with KFP_FLAG_PROFILE, add its kernel times.
   kfp_status launch_iteration(int kind) {
+    NvtxRange r(kind == kInner ? "kfp.iteration.fp32_correction" : "kfp.iteration");
     if (!(flags & KFP_FLAG_NO_GRAPH)) {
       kfp_status rc = build_graph(kind);
       if (rc) return rc;
@@ -1657,10 +1674,16 @@ struct kfp_batch {
       else cudaEventRecord(ev[i], st);
     };
     rec(0);
-    if (prec == KFP_F64) enqueue_passes<double>(st);
-    else enqueue_passes<float>(st);
+    {
+      NvtxRange r("kfp.batch.sweep");
+      if (prec == KFP_F64) enqueue_passes<double>(st);
+      else enqueue_passes<float>(st);
+    }
     rec(1);
-    for (kfp_swr* h : inst) h->enqueue_reductions(st);
+    {
+      NvtxRange r("kfp.batch.exchange_error");
+      for (kfp_swr* h : inst) h->enqueue_reductions(st);
+    }
     rec(2);
   }
 
