@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "kfp_fe_tma.cuh"
 #include "kfp_sweep_tma.cuh"
 
 namespace kfp {
@@ -52,6 +53,9 @@ struct LaunchSet {
   // the first (mode 0) or last (mode 2) pass of every listed unit
   static void edge(int mode, int fmode, unsigned grid, cudaStream_t st, const StreamProblem<T>* probs,
                    const StreamUnit* units, int n);
+  // one pass of the split P1 scheme of Section 6.2 (kfp_fe_tma.cuh), as pass()
+  static void fe_pass(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const TmaMaps& maps,
+                      const TmaArgs<T>& X, const FeArgs& E, int k);
 };
 
 // Rows per ring stage of a shape.

@@ -383,7 +383,8 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
       atomicExch(X.flag, 1);
       return false;
     }
-    if (*(volatile int*)&sm.abort) return false;  // the producer gave up (stage holds no data)
+    // the producer gives up only before a unit's first chunk (that stage then holds no data)
+    if (c == 0 && *(volatile int*)&sm.abort) return false;
     const int l0 = chunk_l0(c);
     const int l1 = l0 + SH::CH - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||

@@ -71,6 +71,12 @@ struct Tma {
     if (sh == 1) return kfp::LaunchSet<T, 1>::stream(fmode, grid, st, probs, P);
     return kfp::LaunchSet<T, 2>::stream(fmode, grid, st, probs, P);
   }
+  static void fe_pass(int sh, int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const kfp::TmaMaps& maps,
+                      const kfp::TmaArgs<T>& X, const kfp::FeArgs& E, int k) {
+    if (sh == 0) kfp::LaunchSet<T, 0>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
+    else if (sh == 1) kfp::LaunchSet<T, 1>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
+    else kfp::LaunchSet<T, 2>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
+  }
   static void edge(int sh, int mode, int fmode, unsigned grid, cudaStream_t st, const kfp::StreamProblem<T>* probs,
                    const kfp::StreamUnit* units, int n) {
     if (sh == 0) kfp::LaunchSet<T, 0>::edge(mode, fmode, grid, st, probs, units, n);
@@ -310,6 +316,7 @@ struct kfp_swr {
   // launch (one per strip in the serial form)
   int persist = 0, persist_grid = 0, nbx = 0;
   int shape = 0;               // tile shape of the TMA-fed sweep (kfp_launch.h)
+  int use_fe_tma = 0;          // split scheme on the TMA-fed pass (kfp_fe_tma.cuh)
   kfp::TmaMaps maps8;          // tensor maps with 8-row boxes (shapes 1 and 2)
   unsigned* done = nullptr;    // [S * nbx] per-unit completion counters, then [S] tickets
   void* sprob = nullptr;       // device StreamProblem<T> of this handle
@@ -419,10 +426,36 @@ struct kfp_swr {
     return A;
   }
 
+  // The split scheme on the TMA-fed pass: one launch per pass, the periodic column
+  // wrap after every pass that leaves a residue.
+  template <typename T>
+  void enqueue_fe_tma(cudaStream_t st) const {
+    kfp::TmaArgs<T> X = tma_args<T>();
+    const kfp::FeArgs E = fe_args();
+    const bool serial = (flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+    const int groups = serial ? g.S : 1;
+    const dim3 grid(nbx_tma(), serial ? 1 : g.S);
+    const kfp::TmaMaps& mp = shape_maps();
+    for (int grp = 0; grp < groups; ++grp) {
+      X.p.strip0 = serial ? grp : 0;
+      Tma<T>::fe_pass(shape, fmode, true, 0, grid, st, mp, X, E, 0);
+      wrap_after_pass<T>(st, 0, X.p.strip0, serial ? 1 : g.S);
+      for (int k = 1; k < g.nt; ++k) {
+        Tma<T>::fe_pass(shape, fmode, !(k & 1), 1, grid, st, mp, X, E, k);
+        wrap_after_pass<T>(st, k, X.p.strip0, serial ? 1 : g.S);
+      }
+      Tma<T>::fe_pass(shape, fmode, !(g.nt & 1), 2, grid, st, mp, X, E, g.nt);
+    }
+  }
+
   template <typename T>
   void enqueue_passes(cudaStream_t st) const {
     if (use_tma) {
       enqueue_passes_tma<T>(st);
+      return;
+    }
+    if (use_fe_tma) {
+      enqueue_fe_tma<T>(st);
       return;
     }
     kfp::PassArgs<T> A = pass_args<T>();
@@ -698,7 +731,7 @@ struct kfp_swr {
   }
 
   kfp_status check_flag() {
-    if (!use_tma) return KFP_OK;
+    if (!use_tma && !use_fe_tma) return KFP_OK;
     int f = 0;
     KFP_CUDA_TRY(cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) return fail(KFP_ETIMEOUT, "a bounded wait in the sweep kernel expired");
@@ -1011,13 +1044,14 @@ kfp_status build_records(kfp_swr* h, const std::vector<double>& coef, const std:
   return KFP_OK;
 }
 
-template <typename T>
-kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
-  Geometry& g = h->g;
+// Forcing mode of the TMA-fed passes: 0 none, 1 one constant-in-time term (pre-scaled;
+// its factor a0 and, on the host, F with column nx canonicalised), 2 one
+// time-dependent term.
+kfp_status forcing_mode(kfp_swr* h, const kfp_swr_problem* pb, double* a0_out, std::vector<double>* Fh_out) {
+  const Geometry& g = h->g;
   const size_t nxp = g.nx + 1;
-  // forcing mode: none, one constant-in-time term (pre-scaled), one time-dependent term
   double a0 = 0.0;
-  std::vector<double> Fh;
+  std::vector<double>& Fh = *Fh_out;
   if (g.nforce == 0) {
     h->fmode = 0;
   } else {
@@ -1036,6 +1070,17 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
         for (int i = 0; i <= g.nv; ++i) Fh[(size_t)i * nxp + g.nx] = Fh[(size_t)i * nxp];
     }
   }
+  *a0_out = a0;
+  return KFP_OK;
+}
+
+template <typename T>
+kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
+  Geometry& g = h->g;
+  double a0 = 0.0;
+  std::vector<double> Fh;
+  kfp_status rc0 = forcing_mode(h, pb, &a0, &Fh);
+  if (rc0) return rc0;
   h->Lpad = g.Lmax + 2 * kfp::kRecPad;
   std::vector<double> coef = build_factors(g);
   std::vector<T> rec, gf;
@@ -1139,6 +1184,104 @@ kfp_status upload_stream_problem(kfp_swr* h) {
 
 kfp_status setup_tma(kfp_swr* h, const kfp_swr_problem* pb) {
   return h->prec == KFP_F64 ? setup_tma_t<double>(h, pb) : setup_tma_t<float>(h, pb);
+}
+
+// Split scheme on the TMA-fed pass: the records of the scaled recurrences
+// (kfp_fe_tma.cuh), [S][2 pass directions][Lpad][3 classes][8], from the current LU
+// factors COEF.  Pass direction d eliminates step k+1 with the factors of direction
+// d (G = g m_off, H = g a) and back-substitutes step k, eliminated the other way; the
+// previous row in pass order is l-1 going up and l+1 going down.
+template <typename T>
+void build_fe_records(const kfp_swr* h, const std::vector<double>& coef, std::vector<T>* out) {
+  const Geometry& g = h->g;
+  const int Lm = g.Lmax, Lpad = h->Lpad;
+  const double m_off = g.hv / 6.0;
+  out->assign((size_t)g.S * 2 * Lpad * kfp::kRecW, T(0));
+  for (int s = 0; s < g.S; ++s) {
+    const kfp::StripInfo& st = g.strips[s];
+    const int L = st.L;
+    for (int d = 0; d < 2; ++d) {
+      const double* cE = &coef[(((size_t)s * 3 + 1) * 2 + d) * 3 * Lm];      // g, coupling, cp
+      const double* cB = &coef[(((size_t)s * 3 + 1) * 2 + (1 - d)) * 3 * Lm];
+      for (int l = 0; l < L; ++l) {
+        const bool first = d == 0 ? l == 0 : l == L - 1;
+        const int prev = d == 0 ? l - 1 : l + 1;
+        const double GB = cB[l] * m_off, GE = cE[l] * m_off;
+        const double kappa = first ? 0.0 : cB[2 * Lm + l] * (cB[prev] * m_off) / GB;
+        const double rho = first ? 0.0 : (cE[l] * cE[Lm + l]) * (cE[prev] * m_off) / GE;
+        const double vi = g.v0 + (st.lo + l) * g.hv;
+        const double c = std::fabs(vi * g.dt / g.hx);
+        for (int cls = 0; cls < 3; ++cls) {
+          T* r = &(*out)[(((size_t)s * 2 + d) * Lpad + kfp::kRecPad + l) * kfp::kRecW + cls * 8];
+          r[0] = (T)(-kappa);
+          r[1] = (T)(GB * (1.0 - c));
+          r[2] = (T)(GB * c);
+          r[3] = (T)(-rho);
+          r[4] = (T)GB;
+          put_bits(&r[6], vi > 0 ? 1 : (vi < 0 ? -1 : 0));
+          put_bits(&r[7], 0);
+        }
+      }
+    }
+  }
+}
+
+// Split scheme on the TMA-fed pass (one forcing term at most): records, the forcing
+// pre-scaled by dt a (one constant-in-time term; both pass directions alike), tensor
+// maps over the scaled residue, u^0, the forcing and the records, and the tile shape.
+template <typename T>
+kfp_status setup_fe_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
+  Geometry& g = h->g;
+  double a0 = 0.0;
+  std::vector<double> Fh;
+  kfp_status rc = forcing_mode(h, pb, &a0, &Fh);
+  if (rc) return rc;
+  h->Lpad = g.Lmax + 2 * kfp::kRecPad;
+  h->Fh_keep = Fh;
+  h->a0_keep = a0;
+  std::vector<T> rec;
+  build_fe_records<T>(h, build_factors(g), &rec);
+  rc = alloc(h, &h->rec, sizeof(T) * rec.size());
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemcpy(h->rec, rec.data(), sizeof(T) * rec.size(), cudaMemcpyHostToDevice));
+  if (h->fmode == 1) {
+    const size_t nxp = g.nx + 1;
+    std::vector<T> gf((size_t)2 * g.rows * g.P, T(0));
+    for (int d = 0; d < 2; ++d)
+      for (int s = 0; s < g.S; ++s) {
+        const kfp::StripInfo& st = g.strips[s];
+        for (int l = 0; l < st.L; ++l) {
+          T* row = &gf[((size_t)d * g.rows + st.rowoff + l) * g.P];
+          for (int m = 0; m <= g.nx; ++m) row[m + 1] = (T)((g.dt * a0) * Fh[(size_t)(st.lo + l) * nxp + m]);
+        }
+      }
+    rc = alloc(h, &h->GF, sizeof(T) * gf.size());
+    if (rc) return rc;
+    KFP_CUDA_TRY_H(cudaMemcpy(h->GF, gf.data(), sizeof(T) * gf.size(), cudaMemcpyHostToDevice));
+  }
+  rc = alloc(h, (void**)&h->flag, sizeof(int));
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemset(h->flag, 0, sizeof(int)));
+  for (int box : {16, 8}) {
+    kfp::TmaMaps& m = box == 16 ? h->maps : h->maps8;
+    rc = encode_2d(h, &m.state, h->Ybuf, (size_t)2 * g.rows, g.P, box, kfp::kBoxW);
+    if (!rc) rc = encode_2d(h, &m.init, h->U0, g.nv + 1, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 1) rc = encode_2d(h, &m.force, h->GF, (size_t)2 * g.rows, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 2) rc = encode_2d(h, &m.force, h->F, g.nv + 1, g.P, box, kfp::kBoxW);
+    if (!rc && h->fmode == 0) m.force = m.init;  // never read
+    if (!rc) rc = encode_2d(h, &m.rec, h->rec, (size_t)g.S * 2 * h->Lpad, kfp::kRecW, box, kfp::kRecW);
+    if (rc) return rc;
+  }
+  cudaError_t e = Tma<T>::set_attrs();
+  if (e != cudaSuccess) return h->fail(KFP_ECUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
+  int sms = 0;
+  KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
+  KFP_CUDA_TRY_H(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const bool serial = (h->flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+  h->shape = requested_shape(h->flags);
+  if (h->shape < 0) h->shape = (serial ? 1 : g.S) * h->nbx_tma() > sms ? 1 : 0;
+  h->use_fe_tma = 1;
+  return KFP_OK;
 }
 
 // Split scheme: the elimination factors scaled for a right-hand side in units of
@@ -1261,6 +1404,8 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
     KFP_CUDA_TRY_H(cudaMemsetAsync(h->zrec, 0, sizeof(double) * nz, h->stream));
     TRY(alloc(h, &h->fe_tab, (size_t)g.S * 2 * 2 * g.Lmax * es));
     TRY(upload_fe_tab(h, build_factors(g)));
+    if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1)
+      TRY(h->prec == KFP_F64 ? setup_fe_tma_t<double>(h, pb) : setup_fe_tma_t<float>(h, pb));
   } else if (!(h->flags & KFP_FLAG_GENERIC) && g.nforce <= 1) {
     rc = setup_tma(h, pb);
     if (rc) return rc;
@@ -1471,6 +1616,11 @@ kfp_status refresh_tables(kfp_swr* h) {
   if (g.split) {
     kfp_status rc = upload_fe_tab(h, coef);
     if (rc) return rc;
+    if (h->use_fe_tma) {
+      std::vector<T> rec;
+      build_fe_records<T>(h, coef, &rec);
+      KFP_CUDA_TRY_H(cudaMemcpy(h->rec, rec.data(), sizeof(T) * rec.size(), cudaMemcpyHostToDevice));
+    }
   }
   if (h->use_tma) {
     std::vector<T> rec, gf;

@@ -399,3 +399,26 @@ def test_split_scheme_set_robin_equals_fresh_handle(overlap, precision):
     if precision == "f64":
         ref = run_oracle(fresh, 3)
         assert rel_max(a[0], ref["u_T"]) <= F64_TOL and rel_max(a[1], ref["lam"]) <= F64_TOL
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,iters", [SPLIT_CASES[0], SPLIT_CASES[3], SPLIT_CASES[5]],
+                         ids=[SPLIT_CASES[0][0], SPLIT_CASES[3][0], SPLIT_CASES[5][0]])
+def test_split_scheme_tile_shapes_are_bitwise_identical(label, factory, iters, precision):
+    """The TMA-fed split-scheme pass gives the same bits in every tile shape (16- or
+    8-row ring stages; its branch-free and row-by-row paths do the same arithmetic)."""
+    prob = factory().replace(neumann_v=True, periodic_x=True, scheme=1)
+    ref = run_gpu(prob, iters, precision, tile_shape=0)
+    for shape in (1, 2):
+        out = run_gpu(prob, iters, precision, tile_shape=shape)
+        for key in ("u_T", "lam", "bands", "hist"):
+            assert np.array_equal(out[key], ref[key]), (shape, key)
+
+
+@pytest.mark.parametrize("label,factory,iters", [SPLIT_CASES[0], SPLIT_CASES[2], SPLIT_CASES[5]],
+                         ids=[SPLIT_CASES[0][0], SPLIT_CASES[2][0], SPLIT_CASES[5][0]])
+def test_split_scheme_plain_kernel_matches_oracle(label, factory, iters):
+    """The plain-load split-scheme pass (taken for two or more forcing terms and with
+    KFP_FLAG_GENERIC) on cases the TMA-fed one normally runs."""
+    prob = factory().replace(neumann_v=True, periodic_x=True, scheme=1)
+    check_f64(run_gpu(prob, iters, "f64", generic=True), run_oracle(prob, iters), prob)
