@@ -223,8 +223,6 @@ __device__ __forceinline__ bool consume_fe_unit(const TmaArgs<T>& X, const FeArg
       atomicExch(X.flag, 1);
       return false;
     }
-    // the producer gives up only before a unit's first chunk (that stage then holds no data)
-    if (c == 0 && *(volatile int*)&sm.abort) return false;
     const int t0 = c * CH;
     // local rows of the chunk and of the row before it (the first row it eliminates)
     const int la = UP ? t0 - 1 : L - t0, lb = UP ? t0 + CH - 1 : L - 1 - (t0 + CH - 1);

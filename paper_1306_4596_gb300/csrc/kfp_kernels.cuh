@@ -238,7 +238,10 @@ __device__ __forceinline__ void block_reduce(double& mx, double& sm) {
 }
 
 // Final step shared by both reductions: the last block to finish combines the
-// per-block partials in block order (deterministic) into result[0..1].
+// per-block partials into result[0..1] in a fixed order -- thread t takes blocks t,
+// t + blockDim, ... in turn, then the fixed shuffle tree of block_reduce -- so that the
+// result does not depend on which block finished last (reproducible bit for bit).
+// out_sum may be NULL (no sum wanted).
 __device__ __forceinline__ bool last_block_combine(double* partial, unsigned* ticket, double mx,
                                                    double sm, double* out_max, double* out_sum) {
   __shared__ bool is_last;
@@ -255,10 +258,7 @@ __device__ __forceinline__ bool last_block_combine(double* partial, unsigned* ti
   double m2 = 0.0, s2 = 0.0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     m2 = nan_max(m2, ((volatile double*)partial)[2 * b + 0]);
-  }
-  // the sum is taken by one thread in block order so that it is reproducible
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < (int)gridDim.x; ++b) s2 += ((volatile double*)partial)[2 * b + 1];
+    if (out_sum) s2 += ((volatile double*)partial)[2 * b + 1];
   }
   block_reduce(m2, s2);
   if (threadIdx.x == 0) {

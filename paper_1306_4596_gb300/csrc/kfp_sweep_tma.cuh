@@ -383,8 +383,6 @@ __device__ __forceinline__ bool consume_unit(const TmaArgs<T>& X, const int k, c
       atomicExch(X.flag, 1);
       return false;
     }
-    // the producer gives up only before a unit's first chunk (that stage then holds no data)
-    if (c == 0 && *(volatile int*)&sm.abort) return false;
     const int l0 = chunk_l0(c);
     const int l1 = l0 + SH::CH - 1;
     const bool rec_chunk = (MODE != 0) && ((rloB <= rhiB && !(l1 < rloB || l0 > rhiB)) ||
@@ -747,6 +745,8 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
       atomicExch(P.flag, 1);
       return;
     }
+    // the producer gives up only before a unit (then this stage holds no data), so
+    // this is the one place the consumers look at the abort word
     if (*(volatile int*)&sm.abort) return;
     if (sm.hdr[q].tail.k < 0) return;
     // copy the header while the stage is held (its first chunk is not released yet);
