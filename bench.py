@@ -58,9 +58,11 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_pass_at_scale.md")
 SWEEP_SOURCE = os.path.join(ROOT, "paper_1306_4596_gb300", "csrc", "kfp_sweep_tma.cuh")
 
 
-def profiled_traffic(dtype: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, or None when the
-    sweep kernel's source has changed since those counters were taken."""
+def profiled_traffic(kernel: str, dtype: str, cells_per_launch: float):
+    """DRAM bytes per launch of KERNEL ("pass" or "stream"): the committed ncu summary's
+    bytes per cell-update times the launch's cell-updates (a pass touches every node
+    once, so traffic grows with the cell-updates), or None when the sweep kernel's
+    source has changed since those counters were taken."""
     import hashlib
     try:
         text = open(PROFILE_SUMMARY).read()
@@ -70,8 +72,8 @@ def profiled_traffic(dtype: str):
     if f"sha256[:16] = {digest}" not in text:
         return None
     for line in text.splitlines():
-        if line.startswith(f"traffic_bytes_per_launch {dtype} = "):
-            return int(line.split("=")[1])
+        if line.startswith(f"traffic_bytes_per_cell_update {kernel} {dtype} = "):
+            return int(round(float(line.split("=")[1]) * cells_per_launch))
     return None
 
 
@@ -284,12 +286,14 @@ def job_rate(world: int, cells_per_iter: int, steps: int, ms: float) -> float:
 
 
 def time_iterations(torch, solver, steps: int, warmup: int, dist, world: int, device_index: int):
-    for _ in range(warmup):
-        solver.sweep(1)
+    # one call, so that a solver that sweeps groups of consecutive iterates builds its
+    # group launches here
+    solver.sweep(warmup)
     stream = torch.cuda.current_stream()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    k0 = solver.pipeline_stats()["kernel_launches"]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(device_index) as clocks:
         start.record(stream)
@@ -299,6 +303,7 @@ def time_iterations(torch, solver, steps: int, warmup: int, dist, world: int, de
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(torch, dist, world, start.elapsed_time(end))
+    solver.timed_kernel_launches = solver.pipeline_stats()["kernel_launches"] - k0
     return ms, clocks.summary()
 
 
@@ -363,12 +368,13 @@ def main():
                          persistent=True if args.persistent else (False if args.per_pass else None))
     ms, clocks = time_iterations(torch, solver, args.steps, args.warmup, dist, world, device_index)
     st = solver.stats()
+    pipe = solver.pipeline_stats()
     iters_total = st["iterations"]
     sweep_ms_per_iter = st["sweep_ms"] / iters_total
-    launches_per_iter = st["launches_per_iter"]
     pass_launches = prob.nt + 1
     avg_pass_ms = sweep_ms_per_iter / pass_launches
     e_hist = solver.error()[3]
+    solver_launches = solver.timed_kernel_launches
     solver.close()
 
     value = job_rate(world, cells_per_iter, args.steps, ms)
@@ -378,22 +384,31 @@ def main():
     hbm = peaks.get("hbm_gbs")
     hbm_label = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
+    # the dominant kernel: the streamed launch of a group of consecutive iterates when
+    # the solver pipelines them, otherwise the per-pass sweep kernel
+    tname = "double" if args.precision == "f64" else "float"
+    if pipe["depth"] > 1 and pipe["stream_launches"] > 0:
+        kern, kern_ms = "stream", pipe["stream_ms"] / pipe["stream_launches"]
+        kern_cells = pipe["stream_cell_updates"] / pipe["stream_launches"]
+        kname = f"sweep_stream_kernel<{tname}> ({pipe['depth']} iterates per launch)"
+    else:
+        kern, kern_ms, kern_cells = "pass", avg_pass_ms, cells_per_pass
+        kname = f"sweep_pass_tma_kernel<{tname}>"
     if args.precision == "f64":
-        achieved = cells_per_pass * FP64_FLOPS_PER_CELL / (avg_pass_ms / 1e3) / 1e12
+        achieved = kern_cells * FP64_FLOPS_PER_CELL / (kern_ms / 1e3) / 1e12
         fp64_peak, fp64_src = fp64_peak_measured(swr_mod, torch)
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": profiled_traffic("f64"),
-                    "peak_source": fp64_src,
-                    "kernel": "sweep_pass_tma_kernel<double>", "avg_launch_ms": avg_pass_ms,
-                    "algorithmic_per_launch": f"{FP64_FLOPS_PER_CELL} flop x {int(cells_per_pass)} cell-updates",
-                    "hbm_view": {"achieved_gbs": cells_per_pass * BYTES_PER_CELL["f64"] / (avg_pass_ms / 1e3) / 1e9,
+                    "frac": achieved / fp64_peak, "traffic": profiled_traffic(kern, "f64", kern_cells),
+                    "peak_source": fp64_src, "kernel": kname, "avg_launch_ms": kern_ms,
+                    "algorithmic_per_launch": f"{FP64_FLOPS_PER_CELL} flop x {int(kern_cells)} cell-updates",
+                    "hbm_view": {"achieved_gbs": kern_cells * BYTES_PER_CELL["f64"] / (kern_ms / 1e3) / 1e9,
                                  "peak_gbs": hbm, "peak_source": hbm_label}}
     else:
-        achieved = cells_per_pass * BYTES_PER_CELL["f32"] / (avg_pass_ms / 1e3) / 1e9
+        achieved = kern_cells * BYTES_PER_CELL["f32"] / (kern_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": profiled_traffic("f32"), "peak_source": hbm_label, "kernel": "sweep_pass_tma_kernel<float>",
-                    "algorithmic_per_launch": f"{BYTES_PER_CELL['f32']} B x {int(cells_per_pass)} cell-updates",
-                    "avg_launch_ms": avg_pass_ms}
+                    "traffic": profiled_traffic(kern, "f32", kern_cells), "peak_source": hbm_label,
+                    "kernel": kname, "avg_launch_ms": kern_ms,
+                    "algorithmic_per_launch": f"{BYTES_PER_CELL['f32']} B x {int(kern_cells)} cell-updates"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -402,9 +417,10 @@ def main():
         "config": {"workload": WORKLOAD if args.nt is None else WORKLOAD.replace("Nt=2000", f"Nt={args.nt}"),
                    "cell_updates_per_step": cells_per_iter,
                    "l2": "state per time step (3 x 68 MB) larger than L2; no flush",
+                   "iterates_per_launch": pipe["depth"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
-        "gpu_launches": launches_per_iter * args.steps,
+        "gpu_launches": solver_launches,
         "clocks": clocks,
         "e_mis_last": float(e_hist[-1, 0]) if len(e_hist) else None,
     }

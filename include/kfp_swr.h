@@ -97,6 +97,20 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
  *   KFP_FLAG_SHAPE(2):  8-row stages, 2 blocks per SM (6 stages FP64, 12 FP32) */
 #define KFP_FLAG_SHAPE_SHIFT 9
 #define KFP_FLAG_SHAPE(n) ((unsigned)((n) + 1) << KFP_FLAG_SHAPE_SHIFT)
+/* Pipelined iterates (parallel form, TMA-fed sweep, no periodic x, nt >= 3): the
+ * sweeps of D consecutive SWR iterates run in one streamed launch as a wavefront
+ * over (iterate, time step) -- iterate d solves step k once iterate d-1 has recorded
+ * the interface data at t^k and t^(k+1) (Section 6.3: each strip reads its
+ * neighbours' previous iterate level by level).  The results of every iterate, the
+ * iteration count at a tolerance and the history are bitwise those of lone
+ * iterations; kfp_swr_sweep computes up to D-1 iterates beyond the one at which a
+ * tolerance is met and discards them.  By default D = 2 x (streamed blocks resident
+ * at once) / (units of a pass), at most 4, and 1 (no pipelining) with
+ * KFP_FLAG_PERSISTENT or KFP_FLAG_PER_PASS; KFP_FLAG_DEPTH(n), n = 1..4, fixes it
+ * (n = 1: none).  Each extra iterate in flight holds its own residue buffers, final
+ * state, overlap bands and interface data (device memory). */
+#define KFP_FLAG_DEPTH_SHIFT 11
+#define KFP_FLAG_DEPTH(n) ((unsigned)(n) << KFP_FLAG_DEPTH_SHIFT)
 #define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each
                                   * step (M + dt S) w = M (u^n + dt f^{n+1}) with P1 elements in v
                                   * (mass M, stiffness S; Robin ends add dt p or dt q to the end row
@@ -201,6 +215,17 @@ kfp_status kfp_swr_solution(kfp_swr_t h, double* dst, int dst_on_device);
 kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_updates_per_iter,
                          int* launches_per_iter, double* sweep_ms, double* exchange_ms,
                          double* error_ms);
+
+/* Launch counters of this handle (all pointers may be NULL): the group size D of
+ * pipelined iterates chosen at create (see KFP_FLAG_DEPTH; 1: no pipelining); the
+ * kernels launched by all sweeps so far (a mixed-precision handle adds those of its
+ * FP32 correction solver); and, over the groups run so far, the number of streamed
+ * launches, the cell-updates those launches computed (the passes of each group's
+ * wavefront that run inside it) and -- with KFP_FLAG_PROFILE -- their summed device
+ * time in milliseconds (CUDA events around each streamed launch).  Synchronises.
+ * Errors: KFP_EINVAL (NULL handle). */
+kfp_status kfp_swr_pipeline_stats(kfp_swr_t h, int* depth, long long* kernel_launches, long long* stream_launches,
+                                  long long* stream_cell_updates, double* stream_ms);
 
 /*
  * Gradient of the interface mismatch after K iterations with respect to the Robin

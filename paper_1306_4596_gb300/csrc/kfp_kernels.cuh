@@ -67,6 +67,9 @@ struct PassArgs {
                                // form) or lam_next (serial form: the strip below, this iterate)
   int strip0;                  // strip of blockIdx.y = 0 (the serial form launches one strip at a time)
   double* lam_next;            // same shape, written by the sweep
+  const double* lam_add;       // NULL, or added to every value written to lam_next (the
+                               // right-hand side d of a correction solve delta = M delta + d,
+                               // TMA-fed sweep only)
   double* bands;               // [S-1][2][nt][ov+1][nx+1]
   T* Y0;                       // [rows][P] elimination residue, even steps
   T* Y1;                       // odd steps

@@ -9,34 +9,37 @@
 
 namespace kfp {
 
-// Exchange: lam_in <- lam_next, e_chg = max |lam_next - lam_in| (trace change).
-// n is even (the data come in pairs of sides), so the arrays are read as 16-byte
-// pairs; four pairs per thread and round are in flight at once.
+// Exchange: e_chg = max |lam_next - lam_prev| (trace change) into *chg, and
+// lam_dst <- lam_next unless lam_dst is NULL.  lam_dst may be lam_prev (each element
+// is read before it is written, by the same thread).  n is even (the data come in
+// pairs of sides), so the arrays are read as 16-byte pairs; four pairs per thread
+// and round are in flight at once.
 __global__ void __launch_bounds__(kReduceThreads)
-exchange_kernel(const double* __restrict__ lam_next, double* __restrict__ lam_in, size_t n,
-                double* partial, unsigned* ticket, double* scal) {
+exchange_kernel(const double* __restrict__ lam_next, const double* lam_prev, double* lam_dst, size_t n,
+                double* partial, unsigned* ticket, double* chg) {
   double mx = 0.0, sm = 0.0;
   const double2* __restrict__ nx2 = reinterpret_cast<const double2*>(lam_next);
-  double2* __restrict__ in2 = reinterpret_cast<double2*>(lam_in);
+  const double2* pv2 = reinterpret_cast<const double2*>(lam_prev);
+  double2* ds2 = reinterpret_cast<double2*>(lam_dst);
   const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e + 3 * stride < n2; e += 4 * stride) {
     double2 a[4], b[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { a[r] = nx2[e + r * stride]; b[r] = in2[e + r * stride]; }
+    for (int r = 0; r < 4; ++r) { a[r] = nx2[e + r * stride]; b[r] = pv2[e + r * stride]; }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       mx = nan_max(mx, nan_max(fabs(a[r].x - b[r].x), fabs(a[r].y - b[r].y)));
-      in2[e + r * stride] = a[r];
+      if (ds2) ds2[e + r * stride] = a[r];
     }
   }
   for (; e < n2; e += stride) {
-    const double2 a = nx2[e], b = in2[e];
+    const double2 a = nx2[e], b = pv2[e];
     mx = nan_max(mx, nan_max(fabs(a.x - b.x), fabs(a.y - b.y)));
-    in2[e] = a;
+    if (ds2) ds2[e] = a;
   }
   block_reduce(mx, sm);
-  last_block_combine(partial, ticket, mx, sm, &scal[1], nullptr);
+  last_block_combine(partial, ticket, mx, sm, chg, nullptr);
 }
 
 // Defect correction on the interface problem (mixed precision).  With G the map of
@@ -82,13 +85,14 @@ __global__ void correct_kernel(double* __restrict__ lam_in, const double* __rest
 }
 
 // Error: e_mis = max |lower - upper| over the overlaps, j_l2 = dt hx sum (lower-upper)^2.
-// Also appends (e_mis, e_chg, j_l2) to the device history.  Element e = j per_side + r
+// Also appends (e_mis, e_chg, j_l2) to the device history, e_chg read from *chg and
+// copied to scal[1].  Element e = j per_side + r
 // of the flat range pairs bands[j][0][r] with bands[j][1][r]; the thread's position
 // is advanced by the grid stride instead of being divided out per element, and four
 // elements per thread and round are in flight at once.
 __global__ void __launch_bounds__(kReduceThreads)
 error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double dthx,
-             double* partial, unsigned* ticket, double* scal, double* hist, int* iter,
+             double* partial, unsigned* ticket, const double* chg, double* scal, double* hist, int* iter,
              int hist_cap, int wrap_nxp) {
   // wrap_nxp = nx + 1 with periodic x (column nx repeats column 0 and is left out of
   // the L2 sum), 0 otherwise
@@ -148,6 +152,7 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
   double emis = 0.0, ssum = 0.0;
   if (last_block_combine(partial, ticket, mx, sm, &emis, &ssum) && threadIdx.x == 0) {
     scal[0] = emis;
+    scal[1] = *chg;
     scal[2] = dthx * ssum;
     const int it = *iter;
     const int slot = it < hist_cap ? it : hist_cap - 1;

@@ -185,7 +185,8 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
       } else {
         lam = (st.p_top + st.q_top) * (double)u - lam_top;
       }
-      A.lam_next[(((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m] = lam;
+      const size_t o = (((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m;
+      A.lam_next[o] = A.lam_add ? lam + A.lam_add[o] : lam;
     }
   }
   if (st.has_bot) {
@@ -203,7 +204,8 @@ __device__ __forceinline__ void record_row(const PassArgs<T>& A, const StripInfo
       } else {
         lam = (st.p_bot + st.q_bot) * (double)u - lam_bot;
       }
-      A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
+      const size_t o = ((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m;
+      A.lam_next[o] = A.lam_add ? lam + A.lam_add[o] : lam;
     }
   }
 }
@@ -594,6 +596,16 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
 // running block: no cycle of waits.  The blocks' rings stay full across unit and
 // pass boundaries, so a unit's start-up latency hides behind the previous unit.
 //
+// Pipelined iterates.  Consecutive SWR iterates of one problem can run in the same
+// launch as a wavefront over (iterate, time step): iterate d of a group reads, in
+// pass k, the interface data at t^k and t^(k+1) that iterate d-1 records in passes k
+// and k+1 (Section 6.3: each strip's data come from its neighbours' previous
+// iterate, time level by time level).  Its unit of slot j runs pass k = j + depth -
+// 2d, so a unit depends only on units of slot j-1: its own strip's (iterate d, pass
+// k-1) and the neighbour strips' (iterate d-1, pass k+1).  The units active in a slot
+// are a contiguous range of the list (iterate-major), and the arithmetic of every
+// iterate is that of a lone iteration, so the results are the same bits.
+//
 // Completion of a unit's pass is a per-unit counter to which every consumer warp
 // adds one after its stores and a proxy fence (no barrier inside the block, so a
 // warp that leaves on an error cannot strand the others).  Every counter wait is
@@ -604,6 +616,8 @@ sweep_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, 
 struct StreamUnit {
   int inst, strip, bx, nc;  // problem, strip, column block, 16-row chunks of the strip (work)
   int left, right;          // list indices of the column neighbours (-1: none)
+  int dep_lo, dep_hi;       // pipelined iterates: the previous iterate's units of strips s-1
+                            // and s+1, same column block (-1: none)
 };
 
 template <typename T>
@@ -612,6 +626,7 @@ struct StreamProblem {
   TmaMaps maps8;   // the same with 8-row boxes
   TmaArgs<T> args;
   int nt, fmode;
+  int lag;         // pipelined iterates: position d of this iterate in its group (0 otherwise)
 };
 
 template <class SH, typename T>
@@ -622,7 +637,10 @@ __device__ __forceinline__ const TmaMaps& maps_for(const StreamProblem<T>& pr) {
 struct StreamArgs {
   const StreamUnit* units;       // sorted by decreasing nt of their problem
   const int* pass_start;         // [npass + 1] first ticket of each interior pass
+  const int* unit_first;         // [npass] list index of the first unit of each pass (NULL: 0)
   int npass;                     // interior passes of the longest problem (max nt - 1)
+  int depth;                     // iterates per pipelined group (1: none); the unit of iterate
+                                 // d in slot j runs pass k = j + depth - 2 d
   int dynamic;                   // 1: tickets from the counter; 0: block b runs unit b of every
                                  // pass (the grid holds the largest pass)
   unsigned* done;                // [units] consumer warps x passes completed (zeroed before)
@@ -686,10 +704,13 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
     int j = 0, sj = -1;
     auto next_ticket = [&]() -> unsigned {
       if (P.dynamic) return atomicAdd(P.ticket, 1u);
-      ++sj;
-      if (sj >= P.npass) return total;
-      const unsigned t = (unsigned)P.pass_start[sj] + blockIdx.x;
-      return t < (unsigned)P.pass_start[sj + 1] ? t : total;  // pass sizes never grow
+      // the next pass that has a unit for this block (pass sizes grow at the start
+      // of a pipelined group and shrink at its end)
+      for (++sj; sj < P.npass; ++sj) {
+        const unsigned t = (unsigned)P.pass_start[sj] + blockIdx.x;
+        if (t < (unsigned)P.pass_start[sj + 1]) return t;
+      }
+      return total;
     };
     unsigned t = next_ticket();
     int last_inst = -1;
@@ -700,9 +721,10 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
         h.k = -1;  // no more work
       } else {
         while ((unsigned)P.pass_start[j + 1] <= t) ++j;
-        const int u = (int)(t - (unsigned)P.pass_start[j]);
+        const int u = (P.unit_first ? P.unit_first[j] : 0) + (int)(t - (unsigned)P.pass_start[j]);
         const StreamUnit un = P.units[u];
-        h.k = j + 1;
+        const int lag = probs[un.inst].lag;
+        h.k = j + P.depth - 2 * lag;
         h.inst = un.inst;
         h.strip = un.strip;
         h.bx = un.bx;
@@ -712,7 +734,14 @@ sweep_stream_kernel(const StreamProblem<T>* __restrict__ probs, const StreamArgs
         const StreamProblem<T>& pr = probs[un.inst];
         h.st = pr.args.p.strips[un.strip];
         h.nc = (h.st.L + SH::CH - 1) / SH::CH;
-        if (j > 0) ok = wait_done(P, u, un.left, un.right, (unsigned)(j * kWarpsPerBlock));
+        // passes of this unit in the launch before this one (a pipelined iterate d
+        // starts in slot d; the passes before its first one ran before the launch)
+        const int jr = j - lag;
+        if (jr > 0) ok = wait_done(P, u, un.left, un.right, (unsigned)(jr * kWarpsPerBlock));
+        // the previous iterate's neighbour strips have finished pass k + 1
+        if (ok && (un.dep_lo >= 0 || un.dep_hi >= 0))
+          ok = wait_done(P, un.dep_lo >= 0 ? un.dep_lo : un.dep_hi, un.dep_lo >= 0 ? un.dep_hi : -1, -1,
+                         (unsigned)((jr + 1) * kWarpsPerBlock));
         if (ok) {
           fence_proxy_async_global();
           const TmaMaps& mp = maps_for<SH>(pr);

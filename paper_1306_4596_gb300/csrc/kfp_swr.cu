@@ -91,6 +91,13 @@ int requested_shape(unsigned flags) {
   return f == 0 ? -1 : f - 1;
 }
 
+// Iterates per pipelined group requested through the flags (-1: choose automatically).
+constexpr int kMaxDepth = 4;
+int requested_depth(unsigned flags) {
+  const int f = (int)((flags >> KFP_FLAG_DEPTH_SHIFT) & 7u);
+  return f == 0 ? -1 : std::min(f, kMaxDepth);
+}
+
 // Return a status with the CUDA error text; OBJ is the handle whose message is set.
 #define KFP_CUDA_TRY_ON(OBJ, call)                                                        \
   do {                                                                                    \
@@ -324,6 +331,27 @@ struct kfp_swr {
   int* spass = nullptr;        // [nt] first ticket of each interior pass (per group)
   int stall_unit = -1;         // self-test only
   unsigned long long wait_ns = 4000000000ull;
+  // pipelined iterates: groups of `depth` consecutive iterates in one streamed launch
+  // (kfp_sweep_tma.cuh); iterates 0..depth-2 of a group write the extra buffers below
+  // (slot d), the last one the handle's own
+  int depth = 1;               // iterates per group (1: every iterate on its own)
+  int pipe_shape = 1, pipe_grid = 0, pipe_ready = 0;
+  void* pipe_Y = nullptr;      // [depth-1][2][rows][P] T
+  void* pipe_UT = nullptr;     // [depth-1][rows][P] T
+  double* pipe_lam = nullptr;  // [depth-1][n_trace] interface data passed between iterates
+  double* pipe_bands = nullptr;  // [depth-1][n_band]
+  std::vector<kfp::TmaMaps> pipe_maps, pipe_maps8;  // [depth-1] maps of the slots' residue buffers
+  unsigned* pipe_done = nullptr;   // [depth * S * nbx] completion counters, then the ticket
+  kfp::StreamUnit* pipe_units = nullptr;  // [depth * S * nbx], iterate-major, strip-major
+  int* pipe_tab = nullptr;     // per group size D = 2..depth: pass_start[nt], unit_first[nt-1]
+  void* pipe_prob = nullptr;   // per group size D = 2..depth: StreamProblem<T>[D]
+  double* grp_chg = nullptr;   // [kMaxDepth] trace change of each iterate of the last group
+  double* grp_host = nullptr;  // pinned [3 * kMaxDepth]
+  cudaGraph_t grp_graph[kMaxDepth + 1] = {};
+  cudaGraphExec_t grp_exec[kMaxDepth + 1] = {};
+  long long stream_launches = 0, stream_cells = 0;  // streamed launches of the groups (profile)
+  long long kernel_launches = 0;  // kernels launched by iterations and groups so far
+  double t_stream = 0;
   kfp::TmaMaps maps;
   void* UT = nullptr;
   void* U0 = nullptr;
@@ -377,7 +405,7 @@ struct kfp_swr {
   double* adj_grad = nullptr;    // [S-1][2]
   int adj_K = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double t_sweep = 0, t_exchange = 0, t_error = 0;
 
   kfp_status fail(kfp_status c, const char* fmt, ...) {
@@ -393,10 +421,20 @@ struct kfp_swr {
   size_t elem() const { return prec == KFP_F64 ? sizeof(double) : sizeof(float); }
   int nbx_tma() const { return (g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock; }  // column blocks per strip
   int launches_per_iter() const {
-    const int groups = (flags & KFP_FLAG_GAUSS_SEIDEL) ? g.S : 1;
-    if (persist) return groups * (g.nt > 1 ? 3 : 2) + 2;
-    return (g.nt + 1 + (g.periodic ? g.nt : 0)) * groups + 2;
+    if (depth > 1) return (group_launches(depth) + depth - 1) / depth;
+    return single_launches(kStandard);
   }
+  // kernel launches of one iteration on its own (the exchange and, outside a
+  // correction solve, the error reduction only with interfaces)
+  int single_launches(int kind) const {
+    const int groups = (flags & KFP_FLAG_GAUSS_SEIDEL) ? g.S : 1;
+    const int passes = persist ? groups * (g.nt > 1 ? 3 : 2) : (g.nt + 1 + (g.periodic ? g.nt : 0)) * groups;
+    return passes + (g.S > 1 ? (kind == 2 ? 1 : 2) : 0);
+  }
+  // kernel launches of one pipelined group of D iterates: the passes before and after
+  // the streamed launch (D (D + 1) / 2 each), the streamed launch, D exchanges and D
+  // error reductions (none in a correction solve)
+  int group_launches(int D) const { return D * (D + 1) + 1 + D + (d_ext ? 0 : D); }
 
   template <typename T>
   kfp::PassArgs<T> pass_args() const {
@@ -419,6 +457,7 @@ struct kfp_swr {
     A.lam_bot_src = (flags & KFP_FLAG_GAUSS_SEIDEL) ? lam_next : lam_in;
     A.strip0 = 0;
     A.lam_next = lam_next;
+    A.lam_add = nullptr;
     A.bands = bands;
     A.Y0 = (T*)Y0;
     A.Y1 = (T*)Y1;
@@ -553,7 +592,9 @@ struct kfp_swr {
     kfp::StreamArgs P;
     P.units = sunits + base;
     P.pass_start = spass;
+    P.unit_first = nullptr;
     P.npass = g.nt - 1;
+    P.depth = 1;
     P.dynamic = (strip < 0 ? g.S * nbx : nbx) > persist_grid ? 1 : 0;
     P.done = done + base;
     P.ticket = done + (size_t)g.S * nbx + (strip < 0 ? 0 : strip);
@@ -624,7 +665,7 @@ struct kfp_swr {
       NvtxRange r("kfp.exchange");
       if (kind == kStandard)
         kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
-            lam_next, lam_in, n_trace, partial, tickets + 0, scal);
+            lam_next, lam_in, lam_in, n_trace, partial, tickets + 0, scal + 1);
       else if (kind == kResidual)
         kfp::residual_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
             lam_next, lam_in, d_res, n_trace, partial, tickets + 0, scal);
@@ -637,7 +678,7 @@ struct kfp_swr {
       NvtxRange r("kfp.error");
       kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
           bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
-          scal, hist, iter, hist_cap, g.periodic ? g.nx + 1 : 0);
+          scal + 1, scal, hist, iter, hist_cap, g.periodic ? g.nx + 1 : 0);
     }
     record(3, st, capturing);
   }
@@ -645,11 +686,119 @@ struct kfp_swr {
   // Exchange + error of one standard iteration (used by the batched form).
   void enqueue_reductions(cudaStream_t st) const {
     if (g.S < 2) return;
-    kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(lam_next, lam_in, n_trace, partial,
-                                                                          tickets + 0, scal);
+    kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(lam_next, lam_in, lam_in, n_trace,
+                                                                          partial, tickets + 0, scal + 1);
     kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
-        bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1, scal, hist, iter,
-        hist_cap, g.periodic ? g.nx + 1 : 0);
+        bands, g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1, scal + 1, scal, hist,
+        iter, hist_cap, g.periodic ? g.nx + 1 : 0);
+  }
+
+  // ---- pipelined iterates -------------------------------------------------------
+  // Iterate d of a group of D reads iter_lam_in(d) and writes iter_lam_next(d, D),
+  // which iterate d+1 reads; the last iterate writes the handle's own lam_next, bands,
+  // residue and final-state buffers, so that after a full group the handle holds its
+  // results exactly as after a lone iteration.
+  size_t ystate_bytes() const { return (size_t)g.rows * g.P * elem(); }
+  double* iter_lam_in(int d) const { return d == 0 ? lam_in : pipe_lam + (size_t)(d - 1) * n_trace; }
+  double* iter_lam_next(int d, int D) const { return d == D - 1 ? lam_next : pipe_lam + (size_t)d * n_trace; }
+  double* iter_bands(int d, int D) const { return d == D - 1 ? bands : pipe_bands + (size_t)d * n_band; }
+  void* iter_UT(int d, int D) const { return d == D - 1 ? UT : (char*)pipe_UT + (size_t)d * ystate_bytes(); }
+  const kfp::TmaMaps& iter_maps(int d, int D, bool rows8) const {
+    if (d == D - 1) return rows8 ? maps8 : maps;
+    return rows8 ? pipe_maps8[d] : pipe_maps[d];
+  }
+  template <typename T>
+  kfp::TmaArgs<T> iter_args(int d, int D) const {
+    kfp::TmaArgs<T> X = tma_args<T>();
+    X.p.lam_in = iter_lam_in(d);
+    X.p.lam_bot_src = X.p.lam_in;
+    X.p.lam_next = iter_lam_next(d, D);
+    X.p.lam_add = d_ext;  // a correction solve folds its right-hand side into the new data
+    X.p.bands = iter_bands(d, D);
+    if (d < D - 1) {
+      char* y = (char*)pipe_Y + (size_t)d * 2 * ystate_bytes();
+      X.p.Y0 = (T*)y;
+      X.p.Y1 = (T*)(y + ystate_bytes());
+    }
+    X.p.UT = (T*)iter_UT(d, D);
+    return X;
+  }
+  // offsets of group size D's slot tables and problem records
+  size_t tab_off(int D) const { return (size_t)(D - 2) * (2 * (size_t)g.nt - 1); }
+  int prob_off(int D) const { return (D - 2) * (D + 1) / 2; }
+  // cell-updates of the passes a group's streamed launch runs (every iterate runs
+  // nt - D of its passes there; a pass advances every node by one step)
+  long long stream_cells_of(int D) const { return g.cells_per_iter / g.nt * (long long)D * (g.nt - D); }
+
+  // The sweeps of D consecutive iterates: pass k of iterate d runs in slot k + 2d, so
+  // that iterate d-1 has recorded the interface data at t^k and t^(k+1) (its passes k
+  // and k+1) before iterate d reads them.  The passes k <= D-1-d (which include the
+  // first passes) run as launches before the streamed launch, the passes k >= nt-d
+  // (which include the last passes) after it, each in slot order.
+  template <typename T>
+  void enqueue_group_passes(cudaStream_t st, bool capturing, int D) const {
+    const int nt = g.nt, SN = g.S * nbx;
+    const dim3 grid(nbx, g.S);
+    const bool r8 = kfp::shape_rows(pipe_shape) == 8;
+    cudaMemsetAsync(pipe_done, 0, sizeof(unsigned) * ((size_t)D * SN + 1), st);
+    for (int slot = 0; slot <= 2 * (D - 1); ++slot)
+      for (int d = 0; d < D; ++d) {
+        const int k = slot - 2 * d;
+        if (k >= 0 && k <= D - 1 - d)
+          Tma<T>::pass(pipe_shape, fmode, !(k & 1), k == 0 ? 0 : 1, grid, st, iter_maps(d, D, r8),
+                       iter_args<T>(d, D), k);
+      }
+    kfp::StreamArgs P;
+    P.units = pipe_units;
+    P.pass_start = pipe_tab + tab_off(D);
+    P.unit_first = P.pass_start + nt;
+    P.npass = nt - 1;
+    P.depth = D;
+    P.dynamic = D * SN > pipe_grid ? 1 : 0;
+    P.done = pipe_done;
+    P.ticket = pipe_done + (size_t)D * SN;
+    P.flag = flag;
+    P.stall_unit = -1;
+    P.wait_ns = wait_ns;
+    record(4, st, capturing);
+    Tma<T>::stream(pipe_shape, fmode, (unsigned)pipe_grid, st,
+                   (const kfp::StreamProblem<T>*)pipe_prob + prob_off(D), P);
+    record(5, st, capturing);
+    for (int slot = nt; slot <= nt + 2 * (D - 1); ++slot)
+      for (int d = 0; d < D; ++d) {
+        const int k = slot - 2 * d;
+        if (k >= nt - d && k <= nt)
+          Tma<T>::pass(pipe_shape, fmode, !(k & 1), k == nt ? 2 : 1, grid, st, iter_maps(d, D, r8),
+                       iter_args<T>(d, D), k);
+      }
+  }
+
+  // One group: the sweeps, then per iterate the trace change (the last iterate's new
+  // data become the current ones) and, outside a correction solve, the error.
+  void enqueue_group(cudaStream_t st, bool capturing, int D) const {
+    record(0, st, capturing);
+    {
+      NvtxRange r("kfp.sweep");
+      if (prec == KFP_F64) enqueue_group_passes<double>(st, capturing, D);
+      else enqueue_group_passes<float>(st, capturing, D);
+    }
+    record(1, st, capturing);
+    {
+      NvtxRange r("kfp.exchange");
+      for (int d = 0; d < D; ++d)
+        kfp::exchange_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+            iter_lam_next(d, D), iter_lam_in(d), d == D - 1 ? lam_in : nullptr, n_trace, partial, tickets + 0,
+            grp_chg + d);
+    }
+    record(2, st, capturing);
+    if (!d_ext) {
+      NvtxRange r("kfp.error");
+      for (int d = 0; d < D; ++d)
+        kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
+            iter_bands(d, D), g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
+            grp_chg + d, scal, hist, iter, hist_cap, 0);
+    }
+    record(3, st, capturing);
   }
 
   template <typename T>
@@ -686,6 +835,12 @@ struct kfp_swr {
       graph_exec[k] = nullptr;
       graph[k] = nullptr;
     }
+    for (int k = 0; k <= kMaxDepth; ++k) {
+      if (grp_exec[k]) cudaGraphExecDestroy(grp_exec[k]);
+      if (grp_graph[k]) cudaGraphDestroy(grp_graph[k]);
+      grp_exec[k] = nullptr;
+      grp_graph[k] = nullptr;
+    }
   }
 
   kfp_status ensure_history(int n) {
@@ -705,6 +860,7 @@ struct kfp_swr {
   // with KFP_FLAG_PROFILE, add its kernel times.
   kfp_status launch_iteration(int kind) {
     NvtxRange r(kind == kInner ? "kfp.iteration.fp32_correction" : "kfp.iteration");
+    kernel_launches += single_launches(kind);
     if (!(flags & KFP_FLAG_NO_GRAPH)) {
       kfp_status rc = build_graph(kind);
       if (rc) return rc;
@@ -721,6 +877,117 @@ struct kfp_swr {
       KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
       t_sweep += a; t_exchange += b; t_error += c;
     }
+    return KFP_OK;
+  }
+
+  // The device records of the groups (unit lists, slot tables, pass arguments of every
+  // iterate), written at the first group: a correction solver learns its right-hand
+  // side only after create.
+  template <typename T>
+  kfp_status upload_pipeline() {
+    const int SN = g.S * nbx, nt = g.nt;
+    std::vector<kfp::StreamUnit> su((size_t)depth * SN);
+    for (int d = 0; d < depth; ++d)
+      for (int s = 0; s < g.S; ++s)
+        for (int bx = 0; bx < nbx; ++bx) {
+          kfp::StreamUnit& un = su[(size_t)d * SN + (size_t)s * nbx + bx];
+          const int n = d * SN + s * nbx + bx;
+          un.inst = d;
+          un.strip = s;
+          un.bx = bx;
+          un.nc = (g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax;
+          un.left = bx > 0 ? n - 1 : -1;
+          un.right = bx + 1 < nbx ? n + 1 : -1;
+          un.dep_lo = (d > 0 && s > 0) ? n - SN - nbx : -1;
+          un.dep_hi = (d > 0 && s + 1 < g.S) ? n - SN + nbx : -1;
+        }
+    // slot j of a group of D holds the units of iterates max(0, j-(nt-1-D)) ..
+    // min(D-1, j), iterate-major
+    std::vector<int> tab((size_t)(depth - 1) * (2 * (size_t)nt - 1));
+    std::vector<kfp::StreamProblem<T>> sp((size_t)prob_off(depth + 1));
+    for (int D = 2; D <= depth; ++D) {
+      int* ps = tab.data() + tab_off(D);
+      int* uf = ps + nt;
+      ps[0] = 0;
+      for (int j = 0; j < nt - 1; ++j) {
+        const int dlo = std::max(0, j - (nt - 1 - D)), dhi = std::min(D - 1, j);
+        uf[j] = dlo * SN;
+        ps[j + 1] = ps[j] + (dhi - dlo + 1) * SN;
+      }
+      for (int d = 0; d < D; ++d) {
+        kfp::StreamProblem<T>& p = sp[(size_t)prob_off(D) + d];
+        std::memset(&p, 0, sizeof p);
+        p.maps = iter_maps(d, D, false);
+        p.maps8 = iter_maps(d, D, true);
+        p.args = iter_args<T>(d, D);
+        p.nt = nt;
+        p.fmode = fmode;
+        p.lag = d;
+      }
+    }
+    KFP_CUDA_TRY(cudaMemcpy(pipe_units, su.data(), sizeof(kfp::StreamUnit) * su.size(), cudaMemcpyHostToDevice));
+    KFP_CUDA_TRY(cudaMemcpy(pipe_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice));
+    KFP_CUDA_TRY(cudaMemcpy(pipe_prob, sp.data(), sizeof(kfp::StreamProblem<T>) * sp.size(), cudaMemcpyHostToDevice));
+    pipe_ready = 1;
+    return KFP_OK;
+  }
+
+  // Launch one group of D >= 2 iterates (graph replay or direct launches).
+  kfp_status launch_group(int D) {
+    NvtxRange r(d_ext ? "kfp.group.fp32_correction" : "kfp.group");
+    if (!pipe_ready) {
+      kfp_status rc = prec == KFP_F64 ? upload_pipeline<double>() : upload_pipeline<float>();
+      if (rc) return rc;
+    }
+    if (!(flags & KFP_FLAG_NO_GRAPH)) {
+      // the graphs of every group size at once, so that the first group of a sweep
+      // builds what its remainder group needs too
+      for (int Dg = 2; Dg <= depth; ++Dg) {
+        if (grp_exec[Dg]) continue;
+        if (!cap_stream) KFP_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        KFP_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_group(cap_stream, true, Dg);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap_stream, &gr);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          return fail(KFP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
+        grp_graph[Dg] = gr;
+        KFP_CUDA_TRY(cudaGraphInstantiate(&grp_exec[Dg], gr, 0));
+        KFP_CUDA_TRY(cudaGraphUpload(grp_exec[Dg], stream));
+      }
+      KFP_CUDA_TRY(cudaGraphLaunch(grp_exec[D], stream));
+    } else {
+      enqueue_group(stream, false, D);
+      KFP_CUDA_TRY(cudaGetLastError());
+    }
+    stream_launches += 1;
+    stream_cells += stream_cells_of(D);
+    kernel_launches += group_launches(D);
+    if (flags & KFP_FLAG_PROFILE) {
+      KFP_CUDA_TRY(cudaEventSynchronize(ev[3]));
+      float a = 0, b = 0, c = 0, q = 0;
+      KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+      KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+      KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
+      KFP_CUDA_TRY(cudaEventElapsedTime(&q, ev[4], ev[5]));
+      t_sweep += a; t_exchange += b; t_error += c; t_stream += q;
+    }
+    return KFP_OK;
+  }
+
+  // Make iterate d of the last group (D iterates) the handle's current one: its new
+  // interface data, bands and final state replace those of the group's last iterate.
+  kfp_status adopt_iterate(int d, int D) {
+    if (d == D - 1) return KFP_OK;
+    KFP_CUDA_TRY(cudaMemcpyAsync(lam_in, iter_lam_next(d, D), sizeof(double) * n_trace, cudaMemcpyDeviceToDevice,
+                                 stream));
+    KFP_CUDA_TRY(cudaMemcpyAsync(lam_next, iter_lam_next(d, D), sizeof(double) * n_trace,
+                                 cudaMemcpyDeviceToDevice, stream));
+    KFP_CUDA_TRY(cudaMemcpyAsync(bands, iter_bands(d, D), sizeof(double) * n_band, cudaMemcpyDeviceToDevice,
+                                 stream));
+    KFP_CUDA_TRY(cudaMemcpyAsync(UT, iter_UT(d, D), ystate_bytes(), cudaMemcpyDeviceToDevice, stream));
     return KFP_OK;
   }
 
@@ -764,7 +1031,38 @@ struct kfp_swr {
     const bool check = tol > 0;
     int done = 0;
     bool converged = false;
-    for (int it = 0; it < max_iters; ++it) {
+    while (done < max_iters) {
+      const int D = std::min(depth, max_iters - done);
+      if (D >= 2) {
+        // a group of D iterates; with a tolerance, the first iterate that meets it
+        // ends the sweep and the later ones are discarded
+        rc = launch_group(D);
+        if (rc) return rc;
+        int stop = -1;
+        if (check) {
+          KFP_CUDA_TRY(cudaMemcpyAsync(grp_host, hist + 3 * (size_t)done, sizeof(double) * 3 * D,
+                                       cudaMemcpyDeviceToHost, stream));
+          KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+          for (int d = 0; d < D && stop < 0; ++d) {
+            const double* r = grp_host + 3 * d;
+            if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2])) {
+              rc = fail(KFP_ENUMERIC, "non-finite interface norm at iteration %lld", iterations + done + d + 1);
+              stop = d;
+            } else if ((tol_kind == 0 ? r[1] : r[0]) < tol) {
+              converged = true;
+              stop = d;
+            }
+          }
+        }
+        if (stop >= 0) {
+          kfp_status ra = adopt_iterate(stop, D);
+          if (ra) return ra;
+          done += stop + 1;
+          break;
+        }
+        done += D;
+        continue;
+      }
       rc = launch_iteration(kStandard);
       if (rc) return rc;
       ++done;
@@ -838,20 +1136,52 @@ struct kfp_swr {
                                    stream));
       double best = INFINITY;
       int since_best = 0, j = 0;
-      for (; j < inner_max; ++j) {
+      const double* delta = inner->lam_in;  // the correction the loop ends with
+      // true when the change chg of an inner iterate ends the loop
+      auto ends = [&](double chg) {
+        if (chg < eta * dnorm) return true;
+        if (chg < 0.5 * best) { best = chg; since_best = 0; }
+        else if (++since_best >= 25) return true;  // stalled at FP32 resolution
+        return false;
+      };
+      while (j < inner_max) {
+        const int D = std::min(inner->depth, inner_max - j);
+        if (D >= 2) {
+          // a group of D inner iterates: the first one whose change ends the loop
+          // gives the correction
+          rc = inner->launch_group(D);
+          if (rc) { last_error = inner->last_error; break; }
+          KFP_CUDA_TRY(cudaMemcpyAsync(inner->grp_host, inner->grp_chg, sizeof(double) * D, cudaMemcpyDeviceToHost,
+                                       stream));
+          KFP_CUDA_TRY(cudaStreamSynchronize(stream));
+          int stop = -1;
+          for (int d = 0; d < D && stop < 0 && !rc; ++d) {
+            const double chg = inner->grp_host[d];
+            if (!std::isfinite(chg)) rc = fail(KFP_ENUMERIC, "non-finite correction");
+            else if (ends(chg)) stop = d;
+          }
+          if (rc) break;
+          if (stop >= 0) {
+            j += stop + 1;
+            delta = inner->iter_lam_next(stop, D);  // iterate stop's delta (the last one: lam_in)
+            if (stop == D - 1) delta = inner->lam_in;
+            break;
+          }
+          j += D;
+          continue;
+        }
         rc = inner->launch_iteration(kInner);
         if (rc) { last_error = inner->last_error; break; }
         rc = inner->read_scalars();
         if (rc) { last_error = inner->last_error; break; }
         const double chg = inner->host_scal[1];
+        ++j;
         if (!std::isfinite(chg)) { rc = fail(KFP_ENUMERIC, "non-finite correction"); break; }
-        if (chg < eta * dnorm) { ++j; break; }
-        if (chg < 0.5 * best) { best = chg; since_best = 0; }
-        else if (++since_best >= 25) { ++j; break; }  // stalled at FP32 resolution
+        if (ends(chg)) break;
       }
       if (rc) break;
       inner_iterations += j;
-      kfp::correct_kernel<<<blocks, 256, 0, stream>>>(lam_in, inner->lam_in, n_trace);
+      kfp::correct_kernel<<<blocks, 256, 0, stream>>>(lam_in, delta, n_trace);
       KFP_CUDA_TRY(cudaGetLastError());
     }
     kfp_status rh = pull_history(done);
@@ -877,12 +1207,14 @@ struct kfp_swr {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    void* bufs[] = {Ybuf, GF, rec, flag, done, sprob, sunits, spass, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
+    void* bufs[] = {Ybuf, GF, rec, flag, done, sprob, sunits, spass, pipe_Y, pipe_UT, pipe_lam, pipe_bands, pipe_done,
+                    pipe_units, pipe_tab, pipe_prob, grp_chg, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, zrec, fe_tab, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
     for (void* b : bufs)
       if (b) cudaFree(b);
     if (host_scal) cudaFreeHost(host_scal);
+    if (grp_host) cudaFreeHost(grp_host);
   }
 };
 
@@ -1154,6 +1486,7 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
           un.nc = (g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax;
           un.left = bx > 0 ? rel - 1 : -1;
           un.right = bx + 1 < nbx ? rel + 1 : -1;
+          un.dep_lo = un.dep_hi = -1;
         }
       const int per_pass = serial ? nbx : (int)nu;
       std::vector<int> ps((size_t)std::max(g.nt, 1));
@@ -1165,6 +1498,79 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
       h->persist = 1;
     }
   }
+  // Pipelined iterates (parallel form, no periodic x): by default when a pass has too
+  // few units for two streamed blocks per resident slot; the buffers are allocated at
+  // the end of create (setup_pipeline).
+  h->nbx = h->nbx_tma();
+  const int dreq = requested_depth(h->flags);
+  if (!serial && !g.periodic && g.S > 1 && g.nt >= 3 && dreq != 1) {
+    const int rs = requested_shape(h->flags);
+    h->pipe_shape = rs >= 0 ? rs : 1;
+    const int pcap = Tma<T>::blocks_per_sm(h->pipe_shape, h->fmode) * sms;
+    int D = dreq;
+    if (D < 0)
+      D = (h->flags & (KFP_FLAG_PERSISTENT | KFP_FLAG_PER_PASS))
+              ? 1
+              : std::max(1, std::min(kMaxDepth, 2 * pcap / std::max(units_per_pass, 1)));
+    D = std::min(D, g.nt - 1);
+    if (D >= 2 && pcap >= 1) {
+      h->depth = D;
+      h->pipe_grid = pcap;
+    }
+  }
+  return KFP_OK;
+}
+
+// Buffers of the pipelined iterates: per extra iterate in flight its residue and
+// final-state buffers, interface data and bands, and the tensor maps of its residue
+// buffers; the counters, unit list, slot tables and problem records of the streamed
+// launches.  If the device memory is not there, the handle runs without pipelining.
+template <typename T>
+kfp_status setup_pipeline(kfp_swr* h) {
+  if (h->depth < 2) return KFP_OK;
+  const Geometry& g = h->g;
+  const int D = h->depth, SN = g.S * h->nbx;
+  const size_t ys = h->ystate_bytes();
+  kfp_status rc = alloc(h, &h->pipe_Y, (size_t)(D - 1) * 2 * ys);
+  if (!rc) rc = alloc(h, &h->pipe_UT, (size_t)(D - 1) * ys);
+  if (!rc) rc = alloc(h, (void**)&h->pipe_lam, sizeof(double) * (D - 1) * h->n_trace);
+  if (!rc) rc = alloc(h, (void**)&h->pipe_bands, sizeof(double) * (D - 1) * std::max<size_t>(h->n_band, 1));
+  if (!rc) rc = alloc(h, (void**)&h->pipe_done, sizeof(unsigned) * ((size_t)D * SN + 1));
+  if (!rc) rc = alloc(h, (void**)&h->pipe_units, sizeof(kfp::StreamUnit) * (size_t)D * SN);
+  if (!rc) rc = alloc(h, (void**)&h->pipe_tab, sizeof(int) * (size_t)(D - 1) * (2 * (size_t)g.nt - 1));
+  if (!rc) rc = alloc(h, &h->pipe_prob, sizeof(kfp::StreamProblem<T>) * (size_t)h->prob_off(D + 1));
+  if (!rc) rc = alloc(h, (void**)&h->grp_chg, sizeof(double) * kMaxDepth);
+  if (rc == KFP_ENOMEM) {
+    // run without pipelining
+    void* bufs[] = {h->pipe_Y, h->pipe_UT, h->pipe_lam, h->pipe_bands, h->pipe_done, h->pipe_units, h->pipe_tab,
+                    h->pipe_prob, h->grp_chg};
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+    h->pipe_Y = h->pipe_UT = h->pipe_prob = nullptr;
+    h->pipe_lam = h->pipe_bands = h->grp_chg = nullptr;
+    h->pipe_done = nullptr;
+    h->pipe_units = nullptr;
+    h->pipe_tab = nullptr;
+    h->depth = 1;
+    h->last_error.clear();
+    return KFP_OK;
+  }
+  if (rc) return rc;
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_Y, 0, (size_t)(D - 1) * 2 * ys, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_UT, 0, (size_t)(D - 1) * ys, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_lam, 0, sizeof(double) * (D - 1) * h->n_trace, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_bands, 0, sizeof(double) * (D - 1) * std::max<size_t>(h->n_band, 1),
+                                 h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->grp_chg, 0, sizeof(double) * kMaxDepth, h->stream));
+  KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->grp_host, sizeof(double) * 3 * kMaxDepth));
+  h->pipe_maps.assign((size_t)D - 1, h->maps);
+  h->pipe_maps8.assign((size_t)D - 1, h->maps8);
+  for (int d = 0; d < D - 1; ++d)
+    for (int box : {16, 8}) {
+      kfp::TmaMaps& m = box == 16 ? h->pipe_maps[d] : h->pipe_maps8[d];
+      rc = encode_2d(h, &m.state, (char*)h->pipe_Y + (size_t)d * 2 * ys, (size_t)2 * g.rows, g.P, box, kfp::kBoxW);
+      if (rc) return rc;
+    }
   return KFP_OK;
 }
 
@@ -1452,6 +1858,9 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream));
   KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->host_scal, sizeof(double) * 3));
   if (h->persist) TRY(h->prec == KFP_F64 ? upload_stream_problem<double>(h) : upload_stream_problem<float>(h));
+  // (a mixed-precision handle runs single FP64 steps; its correction solver pipelines)
+  if (d->prec == KFP_MIXED) h->depth = 1;
+  if (h->use_tma) TRY(h->prec == KFP_F64 ? setup_pipeline<double>(h) : setup_pipeline<float>(h));
   for (auto& e : h->ev) KFP_CUDA_TRY_H(cudaEventCreate(&e));
   KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
   KFP_CUDA_TRY_H(cudaGetLastError());
@@ -1781,7 +2190,9 @@ struct kfp_batch {
     kfp::StreamArgs P;
     P.units = units_dev + grp_begin[fm];
     P.pass_start = pass_dev + grp_pass_off[fm];
+    P.unit_first = nullptr;
     P.npass = grp_npass[fm];
+    P.depth = 1;
     P.dynamic = n > stream_grid ? 1 : 0;  // the first pass is the largest
     P.done = done + grp_begin[fm];
     P.ticket = done + units.size() + fm;
@@ -1975,7 +2386,7 @@ kfp_status batch_setup(kfp_batch* b) {
     const int nbx = h->nbx_tma();
     for (int s = 0; s < h->g.S; ++s)
       for (int bx = 0; bx < nbx; ++bx)
-        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax, -1, -1});
+        b->units.push_back({(int)i, s, bx, (h->g.strips[s].L + kfp::kChunkMax - 1) / kfp::kChunkMax, -1, -1, -1, -1});
   }
   KFP_CUDA_TRY_ON(b, cudaMalloc(&b->probs_dev, sizeof(kfp::StreamProblem<T>) * host.size()));
   KFP_CUDA_TRY_ON(b, cudaMemcpy(b->probs_dev, host.data(), sizeof(kfp::StreamProblem<T>) * host.size(),
@@ -2122,6 +2533,18 @@ kfp_status kfp_swr_stats(kfp_swr_t h, long long* iterations, long long* cell_upd
   return KFP_OK;
 }
 
+kfp_status kfp_swr_pipeline_stats(kfp_swr_t h, int* depth, long long* kernel_launches, long long* stream_launches,
+                                  long long* stream_cell_updates, double* stream_ms) {
+  if (!h) return KFP_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->fail(KFP_ECUDA, "sync failed");
+  if (depth) *depth = h->depth;
+  if (kernel_launches) *kernel_launches = h->kernel_launches + (h->inner ? h->inner->kernel_launches : 0);
+  if (stream_launches) *stream_launches = h->stream_launches;
+  if (stream_cell_updates) *stream_cell_updates = h->stream_cells;
+  if (stream_ms) *stream_ms = h->t_stream;
+  return KFP_OK;
+}
+
 kfp_status kfp_swr_gradient(kfp_swr_t h, int K, const double* lam0, int lam0_on_device, double* J, double* grad_p,
                             double* grad_q) {
   if (!h) return KFP_EINVAL;
@@ -2191,7 +2614,8 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
       break;
     }
     kfp_swr_desc d = descs[i];
-    d.flags &= ~(unsigned)(KFP_FLAG_GENERIC | KFP_FLAG_PROFILE);
+    d.flags &= ~(unsigned)(KFP_FLAG_GENERIC | KFP_FLAG_PROFILE | KFP_FLAG_DEPTH(7));
+    d.flags |= KFP_FLAG_DEPTH(1);  // the batch sweeps its instances one iterate at a time
     kfp_swr_t h = nullptr;
     rc = kfp_swr_create(&d, &probs[i], cuda_stream, &h);
     if (rc) {

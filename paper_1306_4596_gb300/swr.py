@@ -27,12 +27,19 @@ KFP_FLAG_NO_GRAPH, KFP_FLAG_PROFILE, KFP_FLAG_GENERIC, KFP_FLAG_GAUSS_SEIDEL = 1
 KFP_FLAG_NEUMANN_V, KFP_FLAG_PERIODIC_X, KFP_FLAG_SPLIT_SCHEME, KFP_FLAG_PERSISTENT = 16, 32, 64, 128
 KFP_FLAG_PER_PASS = 256
 KFP_FLAG_SHAPE_SHIFT = 9
+KFP_FLAG_DEPTH_SHIFT = 11
 TILE_SHAPES = 3
+MAX_DEPTH = 4
 
 
 def KFP_FLAG_SHAPE(n: int) -> int:
     """Flag fixing the tile shape n (0..2) of the TMA-fed sweep."""
     return (n + 1) << KFP_FLAG_SHAPE_SHIFT
+
+
+def KFP_FLAG_DEPTH(n: int) -> int:
+    """Flag fixing the number n (1..4) of consecutive iterates swept together (1: none)."""
+    return n << KFP_FLAG_DEPTH_SHIFT
 
 
 def problem_flags(prob) -> int:
@@ -98,6 +105,7 @@ def load(rebuild: bool = False):
             lib.kfp_swr_bands.argtypes = [vp, i, i, vp, i]
             lib.kfp_swr_solution.argtypes = [vp, vp, i]
             lib.kfp_swr_stats.argtypes = [vp, llp, llp, ip, _dp, _dp, _dp]
+            lib.kfp_swr_pipeline_stats.argtypes = [vp, ip, llp, llp, llp, _dp]
             lib.kfp_swr_gradient.argtypes = [vp, i, vp, i, _dp, _dp, _dp]
             lib.kfp_swr_gradient.restype = ctypes.c_int
             lib.kfp_swr_set_robin.argtypes = [vp, vp, vp]
@@ -194,6 +202,16 @@ def kfp_swr_stats(h: int) -> dict:
                                    *[ctypes.byref(x) for x in t]))
     return {"iterations": it.value, "cell_updates_per_iter": cells.value, "launches_per_iter": launches.value,
             "sweep_ms": t[0].value, "exchange_ms": t[1].value, "error_ms": t[2].value}
+
+
+def kfp_swr_pipeline_stats(h: int) -> dict:
+    depth = ctypes.c_int()
+    kernels, launches, cells = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(h, load().kfp_swr_pipeline_stats(h, ctypes.byref(depth), ctypes.byref(kernels), ctypes.byref(launches),
+                                            ctypes.byref(cells), ctypes.byref(ms)))
+    return {"depth": depth.value, "kernel_launches": kernels.value, "stream_launches": launches.value,
+            "stream_cell_updates": cells.value, "stream_ms": ms.value}
 
 
 def kfp_swr_counters(h: int) -> dict:
@@ -393,11 +411,14 @@ class SWR:
 
     ``inputs_on`` = "device": the problem arrays are first copied into torch CUDA
     tensors and handed over as device pointers; "host": host (pinned) pointers are
-    handed over and the library copies them in."""
+    handed over and the library copies them in.  ``persistent``, ``tile_shape`` and
+    ``depth`` fix how the sweep is launched (KFP_FLAG_PERSISTENT / KFP_FLAG_PER_PASS,
+    KFP_FLAG_SHAPE, KFP_FLAG_DEPTH); None lets the library choose.  Every choice gives
+    the same bits."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, inputs_on: str = "device",
                  graph: bool = True, profile: bool = False, generic: bool = False, persistent: Optional[bool] = None,
-                 tile_shape: Optional[int] = None):
+                 tile_shape: Optional[int] = None, depth: Optional[int] = None):
         import torch
 
         self.prob = prob
@@ -426,6 +447,7 @@ class SWR:
                  | (KFP_FLAG_GENERIC if generic else 0)
                  | {None: 0, True: KFP_FLAG_PERSISTENT, False: KFP_FLAG_PER_PASS}[persistent]
                  | (0 if tile_shape is None else KFP_FLAG_SHAPE(tile_shape))
+                 | (0 if depth is None else KFP_FLAG_DEPTH(depth))
                  | problem_flags(prob))
         self.desc = kfp_swr_desc(prob.x0, prob.x1, prob.v0, prob.v1, prob.dt, prob.nx, prob.nv, prob.nt, S,
                                  prob.overlap, KFP_ROBIN if prob.robin else KFP_DIRICHLET,
@@ -482,6 +504,9 @@ class SWR:
 
     def stats(self) -> dict:
         return kfp_swr_stats(self.h)
+
+    def pipeline_stats(self) -> dict:
+        return kfp_swr_pipeline_stats(self.h)
 
     def counters(self) -> dict:
         return kfp_swr_counters(self.h)

@@ -87,13 +87,15 @@ def test_profiled_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
     src.write_bytes(b"// kernel v1\n")
     digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     summary = tmp_path / "summary.md"
-    summary.write_text(f"source sha256[:16] = {digest}\ntraffic_bytes_per_launch f64 = 1234\n")
+    summary.write_text(f"source sha256[:16] = {digest}\ntraffic_bytes_per_cell_update stream f64 = 21.5\n"
+                       "traffic_bytes_per_cell_update pass f64 = 20.0\n")
     monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(summary))
     monkeypatch.setattr(bench, "SWEEP_SOURCE", str(src))
-    assert bench.profiled_traffic("f64") == 1234
-    assert bench.profiled_traffic("f32") is None
+    assert bench.profiled_traffic("stream", "f64", 1000) == 21500
+    assert bench.profiled_traffic("pass", "f64", 100) == 2000
+    assert bench.profiled_traffic("stream", "f32", 1000) is None
     src.write_bytes(b"// kernel v2\n")
-    assert bench.profiled_traffic("f64") is None
+    assert bench.profiled_traffic("stream", "f64", 1000) is None
 
 
 def test_job_rate_and_single_rank_time():
