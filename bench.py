@@ -54,7 +54,7 @@ BYTES_PER_CELL = {"f64": 24, "f32": 12}  # read y^k, read F, write y^{k+1}
 FP64_PEAK_TFLOPS_DERIVED = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_pass_at_scale.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sweep_stream_at_scale.md")
 SWEEP_SOURCE = os.path.join(ROOT, "paper_1306_4596_gb300", "csrc", "kfp_sweep_tma.cuh")
 
 
@@ -444,7 +444,7 @@ def main():
         # ---- the other precision ---------------------------------------------------
         other = "f32" if args.precision == "f64" else "f64"
         with swr_mod.SWR(prob, other, inputs_on="device", profile=True) as s:
-            ms2, _ = time_iterations(torch, s, max(args.steps // 3, 3), 1, None, 1, device_index)
+            ms2, _ = time_iterations(torch, s, max(args.steps // 3, 3), 4, None, 1, device_index)
             n2 = max(args.steps // 3, 3)
             st2 = s.stats()
         avg2 = st2["sweep_ms"] / st2["iterations"] / pass_launches
