@@ -59,8 +59,7 @@ __device__ __forceinline__ bool adj_identity(const AdjPassArgs& A, int i, int m,
 // MODE 0: eliminate level nt (no back-substitution); 1: back-substitute level
 // nt-j+1 and eliminate level nt-j; 2: back-substitute level 1 only.
 template <bool UP, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
+__device__ __forceinline__ void adjoint_pass(const AdjPassArgs& A, const int j, const int last_iterate) {
   const int lane = threadIdx.x & 31;
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (w >= A.W) return;  // whole warp leaves together
@@ -231,6 +230,37 @@ adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
     if (t0 >= 1 && t0 + kPrefetch <= L - 1) run_group(BoolTag<true>{}, t0);
     else run_group(BoolTag<false>{}, t0);
   }
+}
+
+template <bool UP, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
+  adjoint_pass<UP, MODE>(A, j, last_iterate);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined iterates of the adjoint: one launch runs, for each iterate z =
+// blockIdx.z of a group, its pass j[z].  Going backward over the iterates, the
+// adjoint of iterate k-1 reads in pass j the lambda_out_bar of levels nt-j and
+// nt-j+1, which the adjoint of iterate k writes in its passes j+1 and j; with pass
+// j of the group's q-th iterate in slot j + 2q, every launch only reads what earlier
+// launches wrote, each iterate has its own residue buffers and lambda_bar slots,
+// and the iterates of one launch add their gradient terms at different levels, in
+// the order of one iterate at a time (bitwise the same sums).
+// ---------------------------------------------------------------------------
+
+constexpr int kAdjGroupMax = 8;
+struct AdjGroup {
+  AdjPassArgs A[kAdjGroupMax];
+  int j[kAdjGroupMax];
+  int last[kAdjGroupMax];
+};
+
+template <bool UP, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adjoint_group_kernel(const __grid_constant__ AdjGroup G) {
+  const int z = blockIdx.z;
+  adjoint_pass<UP, MODE>(G.A[z], G.j[z], G.last[z]);
 }
 
 // grad_p[j] = sum of contrib[j][0] + contrib[j][2]; grad_q[j] = contrib[j][1] + contrib[j][3].

@@ -398,12 +398,13 @@ struct kfp_swr {
   double a0_keep = 0.0;
   // adjoint buffers (allocated by the first kfp_swr_gradient)
   double* adj_bands = nullptr;   // [K][S-1][2][nt][nx+1]
-  double* adj_lbar = nullptr;    // [2][S-1][2][nt][nx+1]
+  double* adj_lbar = nullptr;    // [adj_DA + 1][S-1][2][nt][nx+1] lambda_bar slots
   double* adj_contrib = nullptr; // [S-1][4][nt][nx+1]
-  double* adj_w = nullptr;       // [2][rows][P] elimination residue of the adjoint passes
+  double* adj_w = nullptr;       // [adj_DA][2][rows][P] elimination residue of the adjoint passes
   double* adj_fac = nullptr;     // [S][3][2][3][Lmax] LU factors of A^T
   double* adj_grad = nullptr;    // [S-1][2]
   int adj_K = 0;
+  int adj_DA = 0;                // adjoint iterates in flight the buffers hold
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double t_sweep = 0, t_exchange = 0, t_error = 0;
@@ -1926,12 +1927,24 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   kfp_status rc;
   const size_t ystate = (size_t)g.rows * g.P;
   const size_t nfac = (size_t)g.S * 3 * 2 * 3 * g.Lmax;
-  if (!h->adj_lbar) {
-    if ((rc = alloc(h, (void**)&h->adj_lbar, sizeof(double) * 2 * ntr))) return rc;
+  // adjoint iterates in flight at once (pipelined like the forward sweep unless the
+  // flags ask for one iterate at a time): each has its residue buffers, and the
+  // lambda_bar data passed between them rotate through DA + 1 slots
+  const int DA = requested_depth(h->flags) == 1 ? 1 : std::min(K, kfp::kAdjGroupMax);
+  if (!h->adj_contrib) {
     if ((rc = alloc(h, (void**)&h->adj_contrib, sizeof(double) * (size_t)(g.S - 1) * 4 * per))) return rc;
-    if ((rc = alloc(h, (void**)&h->adj_w, sizeof(double) * 2 * ystate))) return rc;
     if ((rc = alloc(h, (void**)&h->adj_fac, sizeof(double) * nfac))) return rc;
     if ((rc = alloc(h, (void**)&h->adj_grad, sizeof(double) * 2 * (g.S - 1)))) return rc;
+  }
+  if (DA > h->adj_DA) {
+    if (h->adj_lbar) cudaFree(h->adj_lbar);
+    if (h->adj_w) cudaFree(h->adj_w);
+    h->adj_lbar = nullptr;
+    h->adj_w = nullptr;
+    h->adj_DA = 0;
+    if ((rc = alloc(h, (void**)&h->adj_lbar, sizeof(double) * (DA + 1) * ntr))) return rc;
+    if ((rc = alloc(h, (void**)&h->adj_w, sizeof(double) * 2 * (size_t)DA * ystate))) return rc;
+    h->adj_DA = DA;
   }
   if (K > h->adj_K) {
     if (h->adj_bands) cudaFree(h->adj_bands);
@@ -1950,19 +1963,29 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   }
   if ((rc = h->ensure_history(K))) return rc;
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->iter, 0, sizeof(int), h->stream));
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < K;) {
+    const int D = std::min(h->depth, K - k);
+    if (D >= 2) {  // a group of pipelined iterates, each leaving its bands in its own buffer
+      if ((rc = h->launch_group(D))) return rc;
+      for (int d = 0; d < D; ++d)
+        KFP_CUDA_TRY_H(cudaMemcpyAsync(h->adj_bands + (size_t)(k + d) * ntr, h->iter_bands(d, D),
+                                       sizeof(double) * ntr, cudaMemcpyDeviceToDevice, h->stream));
+      k += D;
+      continue;
+    }
     if ((rc = h->launch_iteration(kfp_swr::kStandard))) return rc;
     KFP_CUDA_TRY_H(cudaMemcpyAsync(h->adj_bands + (size_t)k * ntr, h->bands, sizeof(double) * ntr,
                                    cudaMemcpyDeviceToDevice, h->stream));
+    ++k;
   }
   if ((rc = h->pull_history(K))) return rc;
   h->iterations += K;
   if ((rc = h->check_flag())) return rc;
   if (J) *J = h->history[h->history.size() - 1];
   // adjoint, backward over iterates and time levels
-  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_lbar, 0, sizeof(double) * 2 * ntr, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_lbar, 0, sizeof(double) * (DA + 1) * ntr, h->stream));
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_contrib, 0, sizeof(double) * (size_t)(g.S - 1) * 4 * per, h->stream));
-  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_w, 0, sizeof(double) * 2 * ystate, h->stream));
+  KFP_CUDA_TRY_H(cudaMemsetAsync(h->adj_w, 0, sizeof(double) * 2 * (size_t)DA * ystate, h->stream));
   kfp::AdjPassArgs A;
   A.nx = g.nx; A.nv = g.nv; A.nt = g.nt; A.P = g.P; A.W = g.W; A.Lmax = g.Lmax;
   A.two_dt_hv = 2.0 * g.dt / g.hv;
@@ -1974,25 +1997,65 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   A.contrib = h->adj_contrib;
   A.Y0 = h->adj_w;
   A.Y1 = h->adj_w + ystate;
-  double* lb_out = h->adj_lbar;
-  double* lb_in = h->adj_lbar + ntr;
   const dim3 grid((g.W + kfp::kWarpsPerBlock - 1) / kfp::kWarpsPerBlock, g.S);
   const dim3 block(kfp::kWarpsPerBlock * 32);
-  // per iterate, from the last: pass j back-substitutes level nt-j+1 and eliminates
-  // level nt-j, in ascending row order when j is even
-  for (int k = K; k >= 1; --k) {
-    A.bands = h->adj_bands + (size_t)(k - 1) * ntr;
-    A.lbar_out = lb_out;
-    A.lbar_in = lb_in;
-    const int last = k == K ? 1 : 0;
-    kfp::adjoint_pass_kernel<true, 0><<<grid, block, 0, h->stream>>>(A, 0, last);
-    for (int j = 1; j < g.nt; ++j) {
-      if (j & 1) kfp::adjoint_pass_kernel<false, 1><<<grid, block, 0, h->stream>>>(A, j, last);
-      else       kfp::adjoint_pass_kernel<true, 1><<<grid, block, 0, h->stream>>>(A, j, last);
+  // Per iterate, from the last: pass j back-substitutes level nt-j+1 and eliminates
+  // level nt-j, in ascending row order when j is even.  Iterates go in groups of up
+  // to DA; the group's q-th iterate (k = k_hi - q) runs pass j in slot j + 2q, reads
+  // lambda_bar slot (b + q) and writes slot (b + q + 1), modulo DA + 1.
+  const int nring = DA + 1;
+  int b = 0;
+  for (int k_hi = K; k_hi >= 1;) {
+    const int G = std::min(DA, k_hi);
+    kfp::AdjPassArgs Aq[kfp::kAdjGroupMax];
+    for (int q = 0; q < G; ++q) {
+      const int k = k_hi - q;
+      Aq[q] = A;
+      Aq[q].bands = h->adj_bands + (size_t)(k - 1) * ntr;
+      Aq[q].lbar_out = h->adj_lbar + (size_t)((b + q) % nring) * ntr;
+      Aq[q].lbar_in = h->adj_lbar + (size_t)((b + q + 1) % nring) * ntr;
+      Aq[q].Y0 = h->adj_w + (size_t)q * 2 * ystate;
+      Aq[q].Y1 = Aq[q].Y0 + ystate;
     }
-    if (g.nt & 1) kfp::adjoint_pass_kernel<false, 2><<<grid, block, 0, h->stream>>>(A, g.nt, last);
-    else          kfp::adjoint_pass_kernel<true, 2><<<grid, block, 0, h->stream>>>(A, g.nt, last);
-    std::swap(lb_out, lb_in);
+    if (G == 1) {
+      const int last = k_hi == K ? 1 : 0;
+      const kfp::AdjPassArgs& A1 = Aq[0];
+      kfp::adjoint_pass_kernel<true, 0><<<grid, block, 0, h->stream>>>(A1, 0, last);
+      for (int j = 1; j < g.nt; ++j) {
+        if (j & 1) kfp::adjoint_pass_kernel<false, 1><<<grid, block, 0, h->stream>>>(A1, j, last);
+        else       kfp::adjoint_pass_kernel<true, 1><<<grid, block, 0, h->stream>>>(A1, j, last);
+      }
+      if (g.nt & 1) kfp::adjoint_pass_kernel<false, 2><<<grid, block, 0, h->stream>>>(A1, g.nt, last);
+      else          kfp::adjoint_pass_kernel<true, 2><<<grid, block, 0, h->stream>>>(A1, g.nt, last);
+    } else {
+      for (int slot = 0; slot <= g.nt + 2 * (G - 1); ++slot) {
+        // the group's iterates in this slot, by pass kind (first, interior, last)
+        for (int mode = 0; mode < 3; ++mode) {
+          kfp::AdjGroup grp;
+          std::memset(&grp, 0, sizeof grp);
+          int nz = 0;
+          for (int q = 0; q < G; ++q) {
+            const int j = slot - 2 * q;
+            if (j < 0 || j > g.nt) continue;
+            if ((j == 0 ? 0 : (j == g.nt ? 2 : 1)) != mode) continue;
+            grp.A[nz] = Aq[q];
+            grp.j[nz] = j;
+            grp.last[nz] = (k_hi - q) == K ? 1 : 0;
+            ++nz;
+          }
+          if (nz == 0) continue;
+          const dim3 gz(grid.x, grid.y, nz);
+          const bool up = !(slot & 1);  // j = slot - 2q has the parity of the slot
+          if (mode == 0) kfp::adjoint_group_kernel<true, 0><<<gz, block, 0, h->stream>>>(grp);
+          else if (mode == 1 && up) kfp::adjoint_group_kernel<true, 1><<<gz, block, 0, h->stream>>>(grp);
+          else if (mode == 1) kfp::adjoint_group_kernel<false, 1><<<gz, block, 0, h->stream>>>(grp);
+          else if (up) kfp::adjoint_group_kernel<true, 2><<<gz, block, 0, h->stream>>>(grp);
+          else kfp::adjoint_group_kernel<false, 2><<<gz, block, 0, h->stream>>>(grp);
+        }
+      }
+    }
+    b = (b + G) % nring;
+    k_hi -= G;
   }
   kfp::gradient_reduce_kernel<<<2 * (g.S - 1), kfp::kReduceThreads, 0, h->stream>>>(h->adj_contrib, per,
                                                                                      h->adj_grad);

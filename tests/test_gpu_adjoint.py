@@ -103,3 +103,21 @@ def test_gradient_rejects_unsupported():
         with pytest.raises(swr.KfpError) as ei:
             s.gradient(2)
         assert ei.value.status == swr.KFP_ENOTSUP
+
+
+@pytest.mark.parametrize("K", [1, 3, 8, 11])
+@pytest.mark.parametrize("label,factory", CASES[1:], ids=[c[0] for c in CASES[1:]])
+def test_pipelined_adjoint_equals_one_iterate_at_a_time(label, factory, K):
+    """The adjoint iterates in flight together (up to 8 per launch, forward iterates
+    in groups as well) give the bits of one iterate at a time, for K below, at and
+    above the group size."""
+    swr = _swr()
+    prob = factory()
+    with swr.SWR(prob, depth=1) as s:
+        ref = s.gradient(K, prob.lam0)
+    with swr.SWR(prob) as s:
+        got = s.gradient(K, prob.lam0)
+        again = s.gradient(K, prob.lam0)  # buffers reused
+    for a, b, c in zip(ref, got, again):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+        assert np.array_equal(np.asarray(a), np.asarray(c))
