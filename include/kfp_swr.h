@@ -105,10 +105,12 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
  * iteration count at a tolerance and the history are bitwise those of lone
  * iterations; kfp_swr_sweep computes up to D-1 iterates beyond the one at which a
  * tolerance is met and discards them.  By default D = 2 x (streamed blocks resident
- * at once) / (units of a pass), at most 4, and 1 (no pipelining) with
- * KFP_FLAG_PERSISTENT or KFP_FLAG_PER_PASS; KFP_FLAG_DEPTH(n), n = 1..4, fixes it
- * (n = 1: none).  Each extra iterate in flight holds its own residue buffers, final
- * state, overlap bands and interface data (device memory). */
+ * at once) / (units of a pass), at most 8 and at most nt - 1, and 1 (no pipelining)
+ * with KFP_FLAG_PERSISTENT or KFP_FLAG_PER_PASS; KFP_FLAG_DEPTH(n), n = 1..8, fixes
+ * it (n = 1: none; larger n count as 8).  Each extra iterate in flight holds its own
+ * residue buffers, final state, overlap bands and interface data (device memory).
+ * kfp_swr_gradient pipelines its forward iterates the same way and its adjoint
+ * iterates in groups of up to 16 (one at a time with n = 1). */
 #define KFP_FLAG_DEPTH_SHIFT 11
 #define KFP_FLAG_DEPTH(n) ((unsigned)(n) << KFP_FLAG_DEPTH_SHIFT)
 #define KFP_FLAG_SPLIT_SCHEME 64u /* the paper's own discretisation (Section 6.2): Lie splitting, each

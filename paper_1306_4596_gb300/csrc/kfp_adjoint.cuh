@@ -232,15 +232,9 @@ __device__ __forceinline__ void adjoint_pass(const AdjPassArgs& A, const int j, 
   }
 }
 
-template <bool UP, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
-  adjoint_pass<UP, MODE>(A, j, last_iterate);
-}
-
 // ---------------------------------------------------------------------------
-// Pipelined iterates of the adjoint: one launch runs, for each iterate z =
-// blockIdx.z of a group, its pass j[z].  Going backward over the iterates, the
+// One launch runs, for each iterate z = blockIdx.z of a group of pipelined adjoint
+// iterates (one iterate at a time: a group of one), its pass j[z].  Going backward over the iterates, the
 // adjoint of iterate k-1 reads in pass j the lambda_out_bar of levels nt-j and
 // nt-j+1, which the adjoint of iterate k writes in its passes j+1 and j; with pass
 // j of the group's q-th iterate in slot j + 2q, every launch only reads what earlier
@@ -249,7 +243,7 @@ adjoint_pass_kernel(const AdjPassArgs A, const int j, const int last_iterate) {
 // the order of one iterate at a time (bitwise the same sums).
 // ---------------------------------------------------------------------------
 
-constexpr int kAdjGroupMax = 8;
+constexpr int kAdjGroupMax = 16;  // 16 x 120 B of arguments: well inside the parameter space
 struct AdjGroup {
   AdjPassArgs A[kAdjGroupMax];
   int j[kAdjGroupMax];

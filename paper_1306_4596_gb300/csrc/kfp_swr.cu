@@ -92,9 +92,9 @@ int requested_shape(unsigned flags) {
 }
 
 // Iterates per pipelined group requested through the flags (-1: choose automatically).
-constexpr int kMaxDepth = 4;
+constexpr int kMaxDepth = 8;
 int requested_depth(unsigned flags) {
-  const int f = (int)((flags >> KFP_FLAG_DEPTH_SHIFT) & 7u);
+  const int f = (int)((flags >> KFP_FLAG_DEPTH_SHIFT) & 15u);
   return f == 0 ? -1 : std::min(f, kMaxDepth);
 }
 
@@ -1928,9 +1928,11 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
   const size_t ystate = (size_t)g.rows * g.P;
   const size_t nfac = (size_t)g.S * 3 * 2 * 3 * g.Lmax;
   // adjoint iterates in flight at once (pipelined like the forward sweep unless the
-  // flags ask for one iterate at a time): each has its residue buffers, and the
-  // lambda_bar data passed between them rotate through DA + 1 slots
-  const int DA = requested_depth(h->flags) == 1 ? 1 : std::min(K, kfp::kAdjGroupMax);
+  // flags ask for one iterate at a time), in groups of even size: each has its
+  // residue buffers, and the lambda_bar data passed between them rotate through DA + 1
+  // slots
+  const int ngroups = (K + kfp::kAdjGroupMax - 1) / kfp::kAdjGroupMax;
+  const int DA = requested_depth(h->flags) == 1 ? 1 : (K + ngroups - 1) / ngroups;
   if (!h->adj_contrib) {
     if ((rc = alloc(h, (void**)&h->adj_contrib, sizeof(double) * (size_t)(g.S - 1) * 4 * per))) return rc;
     if ((rc = alloc(h, (void**)&h->adj_fac, sizeof(double) * nfac))) return rc;
@@ -2017,41 +2019,29 @@ kfp_status gradient_impl(kfp_swr* h, int K, const double* lam0, int lam0_on_devi
       Aq[q].Y0 = h->adj_w + (size_t)q * 2 * ystate;
       Aq[q].Y1 = Aq[q].Y0 + ystate;
     }
-    if (G == 1) {
-      const int last = k_hi == K ? 1 : 0;
-      const kfp::AdjPassArgs& A1 = Aq[0];
-      kfp::adjoint_pass_kernel<true, 0><<<grid, block, 0, h->stream>>>(A1, 0, last);
-      for (int j = 1; j < g.nt; ++j) {
-        if (j & 1) kfp::adjoint_pass_kernel<false, 1><<<grid, block, 0, h->stream>>>(A1, j, last);
-        else       kfp::adjoint_pass_kernel<true, 1><<<grid, block, 0, h->stream>>>(A1, j, last);
-      }
-      if (g.nt & 1) kfp::adjoint_pass_kernel<false, 2><<<grid, block, 0, h->stream>>>(A1, g.nt, last);
-      else          kfp::adjoint_pass_kernel<true, 2><<<grid, block, 0, h->stream>>>(A1, g.nt, last);
-    } else {
-      for (int slot = 0; slot <= g.nt + 2 * (G - 1); ++slot) {
-        // the group's iterates in this slot, by pass kind (first, interior, last)
-        for (int mode = 0; mode < 3; ++mode) {
-          kfp::AdjGroup grp;
-          std::memset(&grp, 0, sizeof grp);
-          int nz = 0;
-          for (int q = 0; q < G; ++q) {
-            const int j = slot - 2 * q;
-            if (j < 0 || j > g.nt) continue;
-            if ((j == 0 ? 0 : (j == g.nt ? 2 : 1)) != mode) continue;
-            grp.A[nz] = Aq[q];
-            grp.j[nz] = j;
-            grp.last[nz] = (k_hi - q) == K ? 1 : 0;
-            ++nz;
-          }
-          if (nz == 0) continue;
-          const dim3 gz(grid.x, grid.y, nz);
-          const bool up = !(slot & 1);  // j = slot - 2q has the parity of the slot
-          if (mode == 0) kfp::adjoint_group_kernel<true, 0><<<gz, block, 0, h->stream>>>(grp);
-          else if (mode == 1 && up) kfp::adjoint_group_kernel<true, 1><<<gz, block, 0, h->stream>>>(grp);
-          else if (mode == 1) kfp::adjoint_group_kernel<false, 1><<<gz, block, 0, h->stream>>>(grp);
-          else if (up) kfp::adjoint_group_kernel<true, 2><<<gz, block, 0, h->stream>>>(grp);
-          else kfp::adjoint_group_kernel<false, 2><<<gz, block, 0, h->stream>>>(grp);
+    for (int slot = 0; slot <= g.nt + 2 * (G - 1); ++slot) {
+      // the group's iterates in this slot, by pass kind (first, interior, last)
+      for (int mode = 0; mode < 3; ++mode) {
+        kfp::AdjGroup grp;
+        std::memset(&grp, 0, sizeof grp);
+        int nz = 0;
+        for (int q = 0; q < G; ++q) {
+          const int j = slot - 2 * q;
+          if (j < 0 || j > g.nt) continue;
+          if ((j == 0 ? 0 : (j == g.nt ? 2 : 1)) != mode) continue;
+          grp.A[nz] = Aq[q];
+          grp.j[nz] = j;
+          grp.last[nz] = (k_hi - q) == K ? 1 : 0;
+          ++nz;
         }
+        if (nz == 0) continue;
+        const dim3 gz(grid.x, grid.y, nz);
+        const bool up = !(slot & 1);  // j = slot - 2q has the parity of the slot
+        if (mode == 0) kfp::adjoint_group_kernel<true, 0><<<gz, block, 0, h->stream>>>(grp);
+        else if (mode == 1 && up) kfp::adjoint_group_kernel<true, 1><<<gz, block, 0, h->stream>>>(grp);
+        else if (mode == 1) kfp::adjoint_group_kernel<false, 1><<<gz, block, 0, h->stream>>>(grp);
+        else if (up) kfp::adjoint_group_kernel<true, 2><<<gz, block, 0, h->stream>>>(grp);
+        else kfp::adjoint_group_kernel<false, 2><<<gz, block, 0, h->stream>>>(grp);
       }
     }
     b = (b + G) % nring;
@@ -2677,7 +2667,7 @@ kfp_status kfp_batch_create(const kfp_swr_desc* descs, const kfp_swr_problem* pr
       break;
     }
     kfp_swr_desc d = descs[i];
-    d.flags &= ~(unsigned)(KFP_FLAG_GENERIC | KFP_FLAG_PROFILE | KFP_FLAG_DEPTH(7));
+    d.flags &= ~(unsigned)(KFP_FLAG_GENERIC | KFP_FLAG_PROFILE | KFP_FLAG_DEPTH(15));
     d.flags |= KFP_FLAG_DEPTH(1);  // the batch sweeps its instances one iterate at a time
     kfp_swr_t h = nullptr;
     rc = kfp_swr_create(&d, &probs[i], cuda_stream, &h);

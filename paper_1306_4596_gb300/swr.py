@@ -29,7 +29,7 @@ KFP_FLAG_PER_PASS = 256
 KFP_FLAG_SHAPE_SHIFT = 9
 KFP_FLAG_DEPTH_SHIFT = 11
 TILE_SHAPES = 3
-MAX_DEPTH = 4
+MAX_DEPTH = 8
 
 
 def KFP_FLAG_SHAPE(n: int) -> int:
@@ -38,7 +38,7 @@ def KFP_FLAG_SHAPE(n: int) -> int:
 
 
 def KFP_FLAG_DEPTH(n: int) -> int:
-    """Flag fixing the number n (1..4) of consecutive iterates swept together (1: none)."""
+    """Flag fixing the number n (1..8) of consecutive iterates swept together (1: none)."""
     return n << KFP_FLAG_DEPTH_SHIFT
 
 

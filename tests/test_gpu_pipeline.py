@@ -50,12 +50,12 @@ CASES = [
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("label,factory,iters", CASES, ids=[c[0] for c in CASES])
 def test_depths_equal_single_iterates(label, factory, iters, precision):
-    """Groups of 2, 3 and 4 (with partial groups: 5 iterations) give the bits of one
+    """Groups of 2, 3, 4 and 8 (with partial groups: 5 iterations) give the bits of one
     iterate at a time."""
     prob = factory()
     ref = _run(prob, iters, precision, depth=1)
     assert ref["pipe"]["depth"] == 1
-    for D in (2, 3, 4):
+    for D in (2, 3, 4, 8):
         got = _run(prob, iters, precision, depth=D)
         _same(ref, got)
         eff = min(D, prob.nt - 1) if prob.nt >= 3 else 1
