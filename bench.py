@@ -460,8 +460,8 @@ def main():
                                                            {"scheme": 1})):
             mprob = prob.replace(neumann_v=True, periodic_x=True, **kw)
             with swr_mod.SWR(mprob, args.precision, inputs_on="device", profile=True) as s:
-                n3 = 2
-                ms3, _ = time_iterations(torch, s, n3, 1, None, 1, device_index)
+                n3 = 8
+                ms3, _ = time_iterations(torch, s, n3, 4, None, 1, device_index)
                 st3 = s.stats()
             line["variants"].append({"dtype": args.precision, "boundaries": label,
                                      "value": cells_per_iter * n3 / (ms3 / 1e3), "unit": UNIT,

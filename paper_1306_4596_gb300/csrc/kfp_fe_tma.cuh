@@ -145,7 +145,8 @@ __device__ __forceinline__ bool consume_fe_unit(const TmaArgs<T>& X, const FeArg
             } else {
               lam = (st.p_top + st.q_top) * wa - lam_rec_top;
             }
-            A.lam_next[(((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m] = lam;
+            const size_t o = (((size_t)s * 2 + 1) * nt + (k - 1)) * nxp + m;
+            A.lam_next[o] = A.lam_add ? lam + A.lam_add[o] : lam;
           }
         }
         if (st.has_bot) {
@@ -163,7 +164,8 @@ __device__ __forceinline__ bool consume_fe_unit(const TmaArgs<T>& X, const FeArg
             } else {
               lam = (st.p_bot + st.q_bot) * wbeta - lam_rec_bot;
             }
-            A.lam_next[((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m] = lam;
+            const size_t o = ((((size_t)s - 1) * 2 + 0) * nt + (k - 1)) * nxp + m;
+            A.lam_next[o] = A.lam_add ? lam + A.lam_add[o] : lam;
           }
         }
       }
@@ -311,24 +313,36 @@ __device__ __forceinline__ bool consume_fe_unit(const TmaArgs<T>& X, const FeArg
   return true;
 }
 
-// One pass of the split scheme, every unit of the grid (blockIdx.x: column block,
-// blockIdx.y: strip from X.p.strip0); the producer warp streams the scaled residue
-// (or u^0), the pre-scaled forcing and the records through the ring.
+// Passes of the split scheme, one launch per slot of pipelined iterates (as
+// sweep_slot_kernel; one iterate at a time is a slot of one): every unit of the grid
+// (blockIdx.x: column block, blockIdx.y: strip from X.p.strip0, blockIdx.z: iterate);
+// the producer warp streams the scaled residue (or u^0), the pre-scaled forcing and
+// the records through the ring.
+template <typename T>
+struct FeSlotArgs {
+  TmaMaps maps[kSlotMax];
+  TmaArgs<T> X[kSlotMax];
+  FeArgs E[kSlotMax];
+  int k[kSlotMax];
+};
+
 template <typename T, bool UP, int MODE, int FMODE, class SH>
 __global__ void __launch_bounds__((kWarpsPerBlock + 1) * 32, SH::MINB)
-fe_pass_tma_kernel(const __grid_constant__ TmaMaps maps, const TmaArgs<T> X, const FeArgs E, const int k) {
+fe_slot_kernel(const __grid_constant__ FeSlotArgs<T> G) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TmaSmem<T, SH>& sm = *reinterpret_cast<TmaSmem<T, SH>*>(smem_raw);
   init_ring(sm);
+  const int z = blockIdx.z;
+  const TmaArgs<T>& X = G.X[z];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.y + X.p.strip0, bx = blockIdx.x;
   if (warp == kWarpsPerBlock) {
     if (lane != 0) return;
     const StripInfo st = X.p.strips[s];
-    (void)produce_unit<T, UP, MODE, FMODE, SH>(maps, X, k, s, bx, st, sm, 0u, nullptr);
+    (void)produce_unit<T, UP, MODE, FMODE, SH>(G.maps[z], X, G.k[z], s, bx, st, sm, 0u, nullptr);
     return;
   }
-  (void)consume_fe_unit<T, UP, MODE, FMODE, SH>(X, E, k, s, bx, sm, 0u);
+  (void)consume_fe_unit<T, UP, MODE, FMODE, SH>(X, G.E[z], G.k[z], s, bx, sm, 0u);
 }
 
 }  // namespace kfp

@@ -276,7 +276,7 @@ __device__ __forceinline__ bool last_block_combine(double* partial, unsigned* ti
 // column 0, and the ghost columns -1 and nx+1 hold columns nx-1 and 1, so that the
 // halo lanes of the next pass see the wrapped upwind neighbours.  Needs nx >= 2.
 template <typename T>
-__global__ void periodic_wrap_kernel(T* __restrict__ a, int nrows, int P, int nx) {
+__device__ __forceinline__ void periodic_wrap_rows(T* __restrict__ a, int nrows, int P, int nx) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
     T* row = a + (size_t)r * P;
     const T c0 = row[1], c1 = row[2], clast = row[nx];
@@ -284,6 +284,20 @@ __global__ void periodic_wrap_kernel(T* __restrict__ a, int nrows, int P, int nx
     row[nx + 1] = c0;
     row[nx + 2] = c1;
   }
+}
+template <typename T>
+__global__ void periodic_wrap_kernel(T* __restrict__ a, int nrows, int P, int nx) {
+  periodic_wrap_rows(a, nrows, P, nx);
+}
+// The same for up to four arrays at once (blockIdx.y selects one): the pipelined
+// iterates of one slot.
+template <typename T>
+struct WrapGroup {
+  T* a[4];
+};
+template <typename T>
+__global__ void periodic_wrap_group_kernel(const WrapGroup<T> g, int nrows, int P, int nx) {
+  periodic_wrap_rows(g.a[blockIdx.y], nrows, P, nx);
 }
 
 // u(T) assembled from the strips: row i taken from row_of[i] of UT.

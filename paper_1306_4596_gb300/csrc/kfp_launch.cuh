@@ -31,43 +31,73 @@ cudaError_t LaunchSet<T, SHAPE>::set_attrs() {
   set((const void*)sweep_pass_tma_kernel<T, true, 2, 0, SH>);
   set((const void*)sweep_pass_tma_kernel<T, false, 2, 0, SH>);
   set((const void*)edge_pass_kernel<T, 2, 0, SH>);
-#define KFP_SET_FE(FM)                                                    \
-  set((const void*)fe_pass_tma_kernel<T, true, 0, FM, SH>);               \
-  set((const void*)fe_pass_tma_kernel<T, true, 1, FM, SH>);               \
-  set((const void*)fe_pass_tma_kernel<T, false, 1, FM, SH>);
-  KFP_SET_FE(0)
-  KFP_SET_FE(1)
-  KFP_SET_FE(2)
-#undef KFP_SET_FE
-  set((const void*)fe_pass_tma_kernel<T, true, 2, 0, SH>);
-  set((const void*)fe_pass_tma_kernel<T, false, 2, 0, SH>);
+#define KFP_SET_SLOT(FM)                                                  \
+  set((const void*)sweep_slot_kernel<T, true, 0, FM, SH>);                \
+  set((const void*)sweep_slot_kernel<T, true, 1, FM, SH>);                \
+  set((const void*)sweep_slot_kernel<T, false, 1, FM, SH>);               \
+  set((const void*)fe_slot_kernel<T, true, 0, FM, SH>);                   \
+  set((const void*)fe_slot_kernel<T, true, 1, FM, SH>);                   \
+  set((const void*)fe_slot_kernel<T, false, 1, FM, SH>);
+  KFP_SET_SLOT(0)
+  KFP_SET_SLOT(1)
+  KFP_SET_SLOT(2)
+#undef KFP_SET_SLOT
+  set((const void*)sweep_slot_kernel<T, true, 2, 0, SH>);
+  set((const void*)sweep_slot_kernel<T, false, 2, 0, SH>);
+  set((const void*)fe_slot_kernel<T, true, 2, 0, SH>);
+  set((const void*)fe_slot_kernel<T, false, 2, 0, SH>);
   return e;
 }
 
 template <typename T, int SHAPE>
-void LaunchSet<T, SHAPE>::fe_pass(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const TmaMaps& maps,
-                                  const TmaArgs<T>& X, const FeArgs& E, int k) {
+void LaunchSet<T, SHAPE>::slot(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const SlotArgs<T>& G) {
   using SH = typename ShapeOf<T, SHAPE>::type;
   const dim3 block((kWarpsPerBlock + 1) * 32);
   const size_t sm = smem_bytes();
-#define KFP_FE(UP, MODE, FM) fe_pass_tma_kernel<T, UP, MODE, FM, SH><<<grid, block, sm, st>>>(maps, X, E, k)
+#define KFP_SLOT(UP, MODE, FM) sweep_slot_kernel<T, UP, MODE, FM, SH><<<grid, block, sm, st>>>(G)
   if (mode == 2) {
-    if (up) KFP_FE(true, 2, 0);
-    else KFP_FE(false, 2, 0);
+    if (up) KFP_SLOT(true, 2, 0);
+    else KFP_SLOT(false, 2, 0);
   } else if (mode == 0) {
-    if (fmode == 0) KFP_FE(true, 0, 0);
-    else if (fmode == 1) KFP_FE(true, 0, 1);
-    else KFP_FE(true, 0, 2);
+    if (fmode == 0) KFP_SLOT(true, 0, 0);
+    else if (fmode == 1) KFP_SLOT(true, 0, 1);
+    else KFP_SLOT(true, 0, 2);
   } else if (up) {
-    if (fmode == 0) KFP_FE(true, 1, 0);
-    else if (fmode == 1) KFP_FE(true, 1, 1);
-    else KFP_FE(true, 1, 2);
+    if (fmode == 0) KFP_SLOT(true, 1, 0);
+    else if (fmode == 1) KFP_SLOT(true, 1, 1);
+    else KFP_SLOT(true, 1, 2);
   } else {
-    if (fmode == 0) KFP_FE(false, 1, 0);
-    else if (fmode == 1) KFP_FE(false, 1, 1);
-    else KFP_FE(false, 1, 2);
+    if (fmode == 0) KFP_SLOT(false, 1, 0);
+    else if (fmode == 1) KFP_SLOT(false, 1, 1);
+    else KFP_SLOT(false, 1, 2);
   }
-#undef KFP_FE
+#undef KFP_SLOT
+}
+
+template <typename T, int SHAPE>
+void LaunchSet<T, SHAPE>::fe_slot(int fmode, bool up, int mode, dim3 grid, cudaStream_t st,
+                                  const FeSlotArgs<T>& G) {
+  using SH = typename ShapeOf<T, SHAPE>::type;
+  const dim3 block((kWarpsPerBlock + 1) * 32);
+  const size_t sm = smem_bytes();
+#define KFP_FESLOT(UP, MODE, FM) fe_slot_kernel<T, UP, MODE, FM, SH><<<grid, block, sm, st>>>(G)
+  if (mode == 2) {
+    if (up) KFP_FESLOT(true, 2, 0);
+    else KFP_FESLOT(false, 2, 0);
+  } else if (mode == 0) {
+    if (fmode == 0) KFP_FESLOT(true, 0, 0);
+    else if (fmode == 1) KFP_FESLOT(true, 0, 1);
+    else KFP_FESLOT(true, 0, 2);
+  } else if (up) {
+    if (fmode == 0) KFP_FESLOT(true, 1, 0);
+    else if (fmode == 1) KFP_FESLOT(true, 1, 1);
+    else KFP_FESLOT(true, 1, 2);
+  } else {
+    if (fmode == 0) KFP_FESLOT(false, 1, 0);
+    else if (fmode == 1) KFP_FESLOT(false, 1, 1);
+    else KFP_FESLOT(false, 1, 2);
+  }
+#undef KFP_FESLOT
 }
 
 template <typename T, int SHAPE>

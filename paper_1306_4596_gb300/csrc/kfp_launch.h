@@ -53,9 +53,11 @@ struct LaunchSet {
   // the first (mode 0) or last (mode 2) pass of every listed unit
   static void edge(int mode, int fmode, unsigned grid, cudaStream_t st, const StreamProblem<T>* probs,
                    const StreamUnit* units, int n);
-  // one pass of the split P1 scheme of Section 6.2 (kfp_fe_tma.cuh), as pass()
-  static void fe_pass(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const TmaMaps& maps,
-                      const TmaArgs<T>& X, const FeArgs& E, int k);
+  // one slot of pipelined iterates (grid.z = iterates of the slot, all in pass kind
+  // MODE and direction UP), the sweep or the split P1 scheme of Section 6.2
+  // (kfp_fe_tma.cuh; its passes always run here, one iterate at a time as a slot of one)
+  static void slot(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const SlotArgs<T>& G);
+  static void fe_slot(int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const FeSlotArgs<T>& G);
 };
 
 // Rows per ring stage of a shape.

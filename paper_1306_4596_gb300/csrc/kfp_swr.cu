@@ -71,11 +71,16 @@ struct Tma {
     if (sh == 1) return kfp::LaunchSet<T, 1>::stream(fmode, grid, st, probs, P);
     return kfp::LaunchSet<T, 2>::stream(fmode, grid, st, probs, P);
   }
-  static void fe_pass(int sh, int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const kfp::TmaMaps& maps,
-                      const kfp::TmaArgs<T>& X, const kfp::FeArgs& E, int k) {
-    if (sh == 0) kfp::LaunchSet<T, 0>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
-    else if (sh == 1) kfp::LaunchSet<T, 1>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
-    else kfp::LaunchSet<T, 2>::fe_pass(fmode, up, mode, grid, st, maps, X, E, k);
+  static void slot(int sh, int fmode, bool up, int mode, dim3 grid, cudaStream_t st, const kfp::SlotArgs<T>& G) {
+    if (sh == 0) kfp::LaunchSet<T, 0>::slot(fmode, up, mode, grid, st, G);
+    else if (sh == 1) kfp::LaunchSet<T, 1>::slot(fmode, up, mode, grid, st, G);
+    else kfp::LaunchSet<T, 2>::slot(fmode, up, mode, grid, st, G);
+  }
+  static void fe_slot(int sh, int fmode, bool up, int mode, dim3 grid, cudaStream_t st,
+                      const kfp::FeSlotArgs<T>& G) {
+    if (sh == 0) kfp::LaunchSet<T, 0>::fe_slot(fmode, up, mode, grid, st, G);
+    else if (sh == 1) kfp::LaunchSet<T, 1>::fe_slot(fmode, up, mode, grid, st, G);
+    else kfp::LaunchSet<T, 2>::fe_slot(fmode, up, mode, grid, st, G);
   }
   static void edge(int sh, int mode, int fmode, unsigned grid, cudaStream_t st, const kfp::StreamProblem<T>* probs,
                    const kfp::StreamUnit* units, int n) {
@@ -336,6 +341,9 @@ struct kfp_swr {
   // (slot d), the last one the handle's own
   int depth = 1;               // iterates per group (1: every iterate on its own)
   int pipe_shape = 1, pipe_grid = 0, pipe_ready = 0;
+  int pipe_slots = 0;          // 1: one launch per slot of the wavefront (periodic x, split
+                               // scheme), 0: one streamed launch per group
+  double* pipe_zrec = nullptr; // split scheme: [depth-1][2][S][2][2][nx+1] z^k of the slots
   void* pipe_Y = nullptr;      // [depth-1][2][rows][P] T
   void* pipe_UT = nullptr;     // [depth-1][rows][P] T
   double* pipe_lam = nullptr;  // [depth-1][n_trace] interface data passed between iterates
@@ -435,7 +443,25 @@ struct kfp_swr {
   // kernel launches of one pipelined group of D iterates: the passes before and after
   // the streamed launch (D (D + 1) / 2 each), the streamed launch, D exchanges and D
   // error reductions (none in a correction solve)
-  int group_launches(int D) const { return D * (D + 1) + 1 + D + (d_ext ? 0 : D); }
+  int group_launches(int D) const {
+    return (pipe_slots ? slot_launches(D) : D * (D + 1) + 1) + D + (d_ext ? 0 : D);
+  }
+  // launches of the passes of a group run one launch per slot: per slot one per pass
+  // kind present, and with periodic x one column wrap
+  int slot_launches(int D) const {
+    int n = 0;
+    for (int slot = 0; slot <= g.nt + 2 * (D - 1); ++slot) {
+      int has[3] = {0, 0, 0}, wrap = 0;
+      for (int d = 0; d < D; ++d) {
+        const int k = slot - 2 * d;
+        if (k < 0 || k > g.nt) continue;
+        has[k == 0 ? 0 : (k == g.nt ? 2 : 1)] = 1;
+        if (g.periodic && k < g.nt) wrap = 1;
+      }
+      n += has[0] + has[1] + has[2] + wrap;
+    }
+    return n;
+  }
 
   template <typename T>
   kfp::PassArgs<T> pass_args() const {
@@ -476,15 +502,19 @@ struct kfp_swr {
     const int groups = serial ? g.S : 1;
     const dim3 grid(nbx_tma(), serial ? 1 : g.S);
     const kfp::TmaMaps& mp = shape_maps();
+    // the one-iterate slot kernel: the pipelined groups run the same code, so that
+    // they give the same bits
+    kfp::FeSlotArgs<T> F;
+    F.maps[0] = mp;
+    F.E[0] = E;
     for (int grp = 0; grp < groups; ++grp) {
       X.p.strip0 = serial ? grp : 0;
-      Tma<T>::fe_pass(shape, fmode, true, 0, grid, st, mp, X, E, 0);
-      wrap_after_pass<T>(st, 0, X.p.strip0, serial ? 1 : g.S);
-      for (int k = 1; k < g.nt; ++k) {
-        Tma<T>::fe_pass(shape, fmode, !(k & 1), 1, grid, st, mp, X, E, k);
-        wrap_after_pass<T>(st, k, X.p.strip0, serial ? 1 : g.S);
+      F.X[0] = X;
+      for (int k = 0; k <= g.nt; ++k) {
+        F.k[0] = k;
+        Tma<T>::fe_slot(shape, fmode, !(k & 1), k == 0 ? 0 : (k == g.nt ? 2 : 1), grid, st, F);
+        if (k < g.nt) wrap_after_pass<T>(st, k, X.p.strip0, serial ? 1 : g.S);
       }
-      Tma<T>::fe_pass(shape, fmode, !(g.nt & 1), 2, grid, st, mp, X, E, g.nt);
     }
   }
 
@@ -731,6 +761,54 @@ struct kfp_swr {
   // nt - D of its passes there; a pass advances every node by one step)
   long long stream_cells_of(int D) const { return g.cells_per_iter / g.nt * (long long)D * (g.nt - D); }
 
+  kfp::FeArgs iter_fe(int d, int D) const {
+    kfp::FeArgs E = fe_args();
+    if (d < D - 1) E.zrec = pipe_zrec + (size_t)d * 2 * g.S * 2 * 2 * (g.nx + 1);
+    return E;
+  }
+
+  // The same wavefront as enqueue_group_passes with one launch per slot and pass kind
+  // (grid.z = the slot's iterates of that kind), for the forms that need a step
+  // between passes: periodic x wraps the columns of every residue a slot wrote.
+  template <typename T>
+  void enqueue_group_slots(cudaStream_t st, int D) const {
+    const int nt = g.nt;
+    const bool r8 = kfp::shape_rows(pipe_shape) == 8;
+    for (int slot = 0; slot <= nt + 2 * (D - 1); ++slot) {
+      kfp::WrapGroup<T> wg;
+      int nwrap = 0;
+      for (int mode = 0; mode < 3; ++mode) {
+        kfp::SlotArgs<T> G;
+        kfp::FeSlotArgs<T> F;
+        int nz = 0;
+        for (int d = 0; d < D; ++d) {
+          const int k = slot - 2 * d;
+          if (k < 0 || k > nt || (k == 0 ? 0 : (k == nt ? 2 : 1)) != mode) continue;
+          const kfp::TmaArgs<T> X = iter_args<T>(d, D);
+          if (g.split) {
+            F.maps[nz] = iter_maps(d, D, r8);
+            F.X[nz] = X;
+            F.E[nz] = iter_fe(d, D);
+            F.k[nz] = k;
+          } else {
+            G.maps[nz] = iter_maps(d, D, r8);
+            G.X[nz] = X;
+            G.k[nz] = k;
+          }
+          ++nz;
+          if (g.periodic && k < nt) wg.a[nwrap++] = ((k + 1) & 1) ? X.p.Y1 : X.p.Y0;
+        }
+        if (nz == 0) continue;
+        const dim3 grid(nbx, g.S, nz);
+        const bool up = !(slot & 1);  // k = slot - 2d has the parity of the slot
+        if (g.split) Tma<T>::fe_slot(pipe_shape, fmode, up, mode, grid, st, F);
+        else Tma<T>::slot(pipe_shape, fmode, up, mode, grid, st, G);
+      }
+      if (nwrap > 0)
+        kfp::periodic_wrap_group_kernel<T><<<dim3((g.rows + 255) / 256, nwrap), 256, 0, st>>>(wg, g.rows, g.P, g.nx);
+    }
+  }
+
   // The sweeps of D consecutive iterates: pass k of iterate d runs in slot k + 2d, so
   // that iterate d-1 has recorded the interface data at t^k and t^(k+1) (its passes k
   // and k+1) before iterate d reads them.  The passes k <= D-1-d (which include the
@@ -738,6 +816,10 @@ struct kfp_swr {
   // (which include the last passes) after it, each in slot order.
   template <typename T>
   void enqueue_group_passes(cudaStream_t st, bool capturing, int D) const {
+    if (pipe_slots) {
+      enqueue_group_slots<T>(st, D);
+      return;
+    }
     const int nt = g.nt, SN = g.S * nbx;
     const dim3 grid(nbx, g.S);
     const bool r8 = kfp::shape_rows(pipe_shape) == 8;
@@ -797,7 +879,7 @@ struct kfp_swr {
       for (int d = 0; d < D; ++d)
         kfp::error_kernel<<<reduce_blocks, kfp::kReduceThreads, 0, st>>>(
             iter_bands(d, D), g.S - 1, band_per_side, g.dt * g.hx, partial + 2 * reduce_blocks, tickets + 1,
-            grp_chg + d, scal, hist, iter, hist_cap, 0);
+            grp_chg + d, scal, hist, iter, hist_cap, g.periodic ? g.nx + 1 : 0);
     }
     record(3, st, capturing);
   }
@@ -936,7 +1018,7 @@ struct kfp_swr {
   // Launch one group of D >= 2 iterates (graph replay or direct launches).
   kfp_status launch_group(int D) {
     NvtxRange r(d_ext ? "kfp.group.fp32_correction" : "kfp.group");
-    if (!pipe_ready) {
+    if (!pipe_ready && !pipe_slots) {
       kfp_status rc = prec == KFP_F64 ? upload_pipeline<double>() : upload_pipeline<float>();
       if (rc) return rc;
     }
@@ -963,8 +1045,10 @@ struct kfp_swr {
       enqueue_group(stream, false, D);
       KFP_CUDA_TRY(cudaGetLastError());
     }
-    stream_launches += 1;
-    stream_cells += stream_cells_of(D);
+    if (!pipe_slots) {
+      stream_launches += 1;
+      stream_cells += stream_cells_of(D);
+    }
     kernel_launches += group_launches(D);
     if (flags & KFP_FLAG_PROFILE) {
       KFP_CUDA_TRY(cudaEventSynchronize(ev[3]));
@@ -972,7 +1056,7 @@ struct kfp_swr {
       KFP_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
       KFP_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
       KFP_CUDA_TRY(cudaEventElapsedTime(&c, ev[2], ev[3]));
-      KFP_CUDA_TRY(cudaEventElapsedTime(&q, ev[4], ev[5]));
+      if (!pipe_slots) KFP_CUDA_TRY(cudaEventElapsedTime(&q, ev[4], ev[5]));
       t_sweep += a; t_exchange += b; t_error += c; t_stream += q;
     }
     return KFP_OK;
@@ -1208,7 +1292,8 @@ struct kfp_swr {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    void* bufs[] = {Ybuf, GF, rec, flag, done, sprob, sunits, spass, pipe_Y, pipe_UT, pipe_lam, pipe_bands, pipe_done,
+    void* bufs[] = {Ybuf, GF, rec, flag, done, sprob, sunits, spass, pipe_Y, pipe_UT, pipe_lam, pipe_bands, pipe_zrec,
+                    pipe_done,
                     pipe_units, pipe_tab, pipe_prob, grp_chg, UT, U0, F, coef, cabs, sgn, strips, row_of, dta, bc_xin, bc_v,
                     lam_in, lam_next, bands, zrec, fe_tab, partial, tickets, scal, hist, iter, stage, d_res,
                     adj_bands, adj_lbar, adj_contrib, adj_w, adj_fac, adj_grad};
@@ -1407,6 +1492,35 @@ kfp_status forcing_mode(kfp_swr* h, const kfp_swr_problem* pb, double* a0_out, s
   return KFP_OK;
 }
 
+// Iterates per pipelined group (parallel form, nt >= 3, interfaces): the flag's value,
+// or by default as many as give two blocks per resident slot of the device (streamed)
+// or one wave of the grid (one launch per slot: its blocks do not persist, and a
+// second, partial wave measured no faster), at most kMaxDepth (kSlotMax) -- none with
+// the explicit launch forms KFP_FLAG_PERSISTENT / KFP_FLAG_PER_PASS.
+template <typename T>
+void choose_depth(kfp_swr* h, int sms, int units_per_pass) {
+  const Geometry& g = h->g;
+  h->depth = 1;
+  h->nbx = h->nbx_tma();
+  const int dreq = requested_depth(h->flags);
+  if ((h->flags & KFP_FLAG_GAUSS_SEIDEL) || g.S < 2 || g.nt < 3 || dreq == 1) return;
+  const int rs = requested_shape(h->flags);
+  h->pipe_shape = rs >= 0 ? rs : 1;
+  const int pcap = Tma<T>::blocks_per_sm(h->pipe_shape, h->fmode) * sms;
+  if (pcap < 1) return;
+  const int dmax = h->pipe_slots ? kfp::kSlotMax : kMaxDepth;
+  int D = dreq;
+  if (D < 0)
+    D = (h->flags & (KFP_FLAG_PERSISTENT | KFP_FLAG_PER_PASS))
+            ? 1
+            : (h->pipe_slots ? 1 : 2) * pcap / std::max(units_per_pass, 1);
+  D = std::min(std::min(D, dmax), g.nt - 1);
+  if (D >= 2) {
+    h->depth = D;
+    h->pipe_grid = pcap;
+  }
+}
+
 template <typename T>
 kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
   Geometry& g = h->g;
@@ -1499,26 +1613,11 @@ kfp_status setup_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
       h->persist = 1;
     }
   }
-  // Pipelined iterates (parallel form, no periodic x): by default when a pass has too
-  // few units for two streamed blocks per resident slot; the buffers are allocated at
-  // the end of create (setup_pipeline).
-  h->nbx = h->nbx_tma();
-  const int dreq = requested_depth(h->flags);
-  if (!serial && !g.periodic && g.S > 1 && g.nt >= 3 && dreq != 1) {
-    const int rs = requested_shape(h->flags);
-    h->pipe_shape = rs >= 0 ? rs : 1;
-    const int pcap = Tma<T>::blocks_per_sm(h->pipe_shape, h->fmode) * sms;
-    int D = dreq;
-    if (D < 0)
-      D = (h->flags & (KFP_FLAG_PERSISTENT | KFP_FLAG_PER_PASS))
-              ? 1
-              : std::max(1, std::min(kMaxDepth, 2 * pcap / std::max(units_per_pass, 1)));
-    D = std::min(D, g.nt - 1);
-    if (D >= 2 && pcap >= 1) {
-      h->depth = D;
-      h->pipe_grid = pcap;
-    }
-  }
+  // Pipelined iterates: streamed, or one launch per slot with periodic x (its column
+  // wrap runs between passes); the buffers are allocated at the end of create
+  // (setup_pipeline).
+  h->pipe_slots = g.periodic ? 1 : 0;
+  choose_depth<T>(h, sms, units_per_pass);
   return KFP_OK;
 }
 
@@ -1532,23 +1631,27 @@ kfp_status setup_pipeline(kfp_swr* h) {
   const Geometry& g = h->g;
   const int D = h->depth, SN = g.S * h->nbx;
   const size_t ys = h->ystate_bytes();
+  const size_t nzr = g.split ? (size_t)2 * g.S * 2 * 2 * (g.nx + 1) : 0;
   kfp_status rc = alloc(h, &h->pipe_Y, (size_t)(D - 1) * 2 * ys);
   if (!rc) rc = alloc(h, &h->pipe_UT, (size_t)(D - 1) * ys);
   if (!rc) rc = alloc(h, (void**)&h->pipe_lam, sizeof(double) * (D - 1) * h->n_trace);
   if (!rc) rc = alloc(h, (void**)&h->pipe_bands, sizeof(double) * (D - 1) * std::max<size_t>(h->n_band, 1));
-  if (!rc) rc = alloc(h, (void**)&h->pipe_done, sizeof(unsigned) * ((size_t)D * SN + 1));
-  if (!rc) rc = alloc(h, (void**)&h->pipe_units, sizeof(kfp::StreamUnit) * (size_t)D * SN);
-  if (!rc) rc = alloc(h, (void**)&h->pipe_tab, sizeof(int) * (size_t)(D - 1) * (2 * (size_t)g.nt - 1));
-  if (!rc) rc = alloc(h, &h->pipe_prob, sizeof(kfp::StreamProblem<T>) * (size_t)h->prob_off(D + 1));
+  if (!rc && nzr) rc = alloc(h, (void**)&h->pipe_zrec, sizeof(double) * (D - 1) * nzr);
+  if (!rc && !h->pipe_slots) {  // the streamed launch's counters, units, tables and records
+    rc = alloc(h, (void**)&h->pipe_done, sizeof(unsigned) * ((size_t)D * SN + 1));
+    if (!rc) rc = alloc(h, (void**)&h->pipe_units, sizeof(kfp::StreamUnit) * (size_t)D * SN);
+    if (!rc) rc = alloc(h, (void**)&h->pipe_tab, sizeof(int) * (size_t)(D - 1) * (2 * (size_t)g.nt - 1));
+    if (!rc) rc = alloc(h, &h->pipe_prob, sizeof(kfp::StreamProblem<T>) * (size_t)h->prob_off(D + 1));
+  }
   if (!rc) rc = alloc(h, (void**)&h->grp_chg, sizeof(double) * kMaxDepth);
   if (rc == KFP_ENOMEM) {
     // run without pipelining
-    void* bufs[] = {h->pipe_Y, h->pipe_UT, h->pipe_lam, h->pipe_bands, h->pipe_done, h->pipe_units, h->pipe_tab,
-                    h->pipe_prob, h->grp_chg};
+    void* bufs[] = {h->pipe_Y, h->pipe_UT, h->pipe_lam, h->pipe_bands, h->pipe_zrec, h->pipe_done, h->pipe_units,
+                    h->pipe_tab, h->pipe_prob, h->grp_chg};
     for (void* b : bufs)
       if (b) cudaFree(b);
     h->pipe_Y = h->pipe_UT = h->pipe_prob = nullptr;
-    h->pipe_lam = h->pipe_bands = h->grp_chg = nullptr;
+    h->pipe_lam = h->pipe_bands = h->grp_chg = h->pipe_zrec = nullptr;
     h->pipe_done = nullptr;
     h->pipe_units = nullptr;
     h->pipe_tab = nullptr;
@@ -1563,6 +1666,7 @@ kfp_status setup_pipeline(kfp_swr* h) {
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_bands, 0, sizeof(double) * (D - 1) * std::max<size_t>(h->n_band, 1),
                                  h->stream));
   KFP_CUDA_TRY_H(cudaMemsetAsync(h->grp_chg, 0, sizeof(double) * kMaxDepth, h->stream));
+  if (nzr) KFP_CUDA_TRY_H(cudaMemsetAsync(h->pipe_zrec, 0, sizeof(double) * (D - 1) * nzr, h->stream));
   KFP_CUDA_TRY_H(cudaMallocHost((void**)&h->grp_host, sizeof(double) * 3 * kMaxDepth));
   h->pipe_maps.assign((size_t)D - 1, h->maps);
   h->pipe_maps8.assign((size_t)D - 1, h->maps8);
@@ -1685,9 +1789,13 @@ kfp_status setup_fe_tma_t(kfp_swr* h, const kfp_swr_problem* pb) {
   KFP_CUDA_TRY_H(cudaGetDevice(&h->device));
   KFP_CUDA_TRY_H(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const bool serial = (h->flags & KFP_FLAG_GAUSS_SEIDEL) != 0;
+  const int units_per_pass = (serial ? 1 : g.S) * h->nbx_tma();
   h->shape = requested_shape(h->flags);
-  if (h->shape < 0) h->shape = (serial ? 1 : g.S) * h->nbx_tma() > sms ? 1 : 0;
+  if (h->shape < 0) h->shape = units_per_pass > sms ? 1 : 0;
   h->use_fe_tma = 1;
+  // pipelined iterates, one launch per slot (the passes are not streamed)
+  h->pipe_slots = 1;
+  choose_depth<T>(h, sms, units_per_pass);
   return KFP_OK;
 }
 
@@ -1861,7 +1969,8 @@ kfp_status create_impl(kfp_swr* h, const kfp_swr_desc* d, const kfp_swr_problem*
   if (h->persist) TRY(h->prec == KFP_F64 ? upload_stream_problem<double>(h) : upload_stream_problem<float>(h));
   // (a mixed-precision handle runs single FP64 steps; its correction solver pipelines)
   if (d->prec == KFP_MIXED) h->depth = 1;
-  if (h->use_tma) TRY(h->prec == KFP_F64 ? setup_pipeline<double>(h) : setup_pipeline<float>(h));
+  if (h->use_tma || h->use_fe_tma)
+    TRY(h->prec == KFP_F64 ? setup_pipeline<double>(h) : setup_pipeline<float>(h));
   for (auto& e : h->ev) KFP_CUDA_TRY_H(cudaEventCreate(&e));
   KFP_CUDA_TRY_H(cudaStreamSynchronize(h->stream));
   KFP_CUDA_TRY_H(cudaGetLastError());

@@ -130,3 +130,58 @@ def test_default_depth_fills_the_device_on_the_at_scale_grid():
         assert s.pipeline_stats()["depth"] == 1
     with swr.SWR(prob, persistent=True) as s:
         assert s.pipeline_stats()["depth"] == 1
+
+
+# The paper's model problem (zero flux in v, periodic x; Section 6.1), with this
+# library's scheme and with the split P1 scheme of Section 6.2: the periodic column
+# wrap runs between passes, so groups run one launch per slot (grid.z = iterate).
+MODEL_CASES = [
+    ("model_robin_S4", lambda: RD(119, 256, 6, 0.002, 4, 0, True, p=5.0, seed=60, nforce=1), 0),
+    ("model_dirichlet_ov4", lambda: RD(30, 128, 5, 0.003, 2, 4, False, seed=62, nforce=0), 0),
+    ("model_bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=67), 0),
+    ("split_robin_S4_pq", lambda: RD(61, 64, 5, 0.005, 4, 0, True, p=3.0, q=1.5, seed=70, nforce=1), 1),
+    ("split_robin_S4_ov1", lambda: RD(119, 128, 4, 0.003, 4, 1, True, p=5.0, q=2.0, seed=73, nforce=1), 1),
+    ("split_bumps_8_strips", lambda: inputs.gaussian_bumps(300, 512, 40, 8e-4, 8, p=4.0, seed=75), 1),
+]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("label,factory,scheme", MODEL_CASES, ids=[c[0] for c in MODEL_CASES])
+def test_slot_launched_groups_equal_single_iterates(label, factory, scheme, precision):
+    prob = factory().replace(neumann_v=True, periodic_x=True, scheme=scheme)
+    ref = _run(prob, 5, precision, depth=1)
+    for D in (2, 3, 4):
+        got = _run(prob, 5, precision, depth=D)
+        _same(ref, got)
+        assert got["pipe"]["depth"] == min(D, prob.nt - 1)
+        assert got["pipe"]["stream_launches"] == 0  # one launch per slot, no streamed launch
+    assert np.array_equal(ref["u_T"][:, prob.nx], ref["u_T"][:, 0])
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_slot_launched_groups_stop_inside_a_group(scheme):
+    prob = RD(90, 256, 12, 0.002, 4, 2, True, p=5.0, seed=88, nforce=1, boundary_data=False).replace(
+        neumann_v=True, periodic_x=True, scheme=scheme)
+    v = _run(prob, 12, depth=1)["hist"][:, 1]
+    assert v[5] < v[:5].min(), v
+    tol = 0.5 * (v[5] + v[:5].min())
+    a = _run(prob, 40, tol=tol, cont=3, depth=1)
+    b = _run(prob, 40, tol=tol, cont=3, depth=4)
+    assert a["n"] == b["n"] == 6
+    _same(a, b)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_mixed_precision_model_problem_pipelined(scheme):
+    """The FP32 correction solver on the model problem, in slot-launched groups."""
+    prob = inputs.gaussian_bumps(128, 256, 60, 1.6e-3, 8, p=4.0, seed=91).replace(
+        neumann_v=True, periodic_x=True, scheme=scheme)
+    from paper_1306_4596_gb300 import swr
+    out = []
+    for D in (1, 4):
+        with swr.SWR(prob, "mixed", depth=D) as s:
+            n = s.sweep(8, 1e-10, 1)
+            out.append({"n": n, "u_T": s.solution(), "lam": s.traces(), "bands": s.bands(),
+                        "hist": s.error()[3], "cnt": s.counters()})
+    _same(out[0], out[1])
+    assert out[0]["cnt"]["fp32_iterations"] == out[1]["cnt"]["fp32_iterations"]
