@@ -27,7 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "kfp_fe.cuh"
-#include "kfp_sweep_tma.cuh"
+#include "kfp_slot.cuh"
 
 namespace kfp {
 

@@ -14,6 +14,7 @@
 #include <stddef.h>
 
 #include "kfp_fe_tma.cuh"
+#include "kfp_slot.cuh"
 #include "kfp_sweep_tma.cuh"
 
 namespace kfp {
