@@ -400,12 +400,10 @@ struct kfp_swr {
   const double* d_ext = nullptr;
   long long inner_iterations = 0;
   int inner_max = 4000;
-  // Tightest relative change an inner solve is asked for.  One FP32 correction leaves
-  // a residual of about 1e-5 |d| however far its iterations go (its rounding); further
-  // iterations still shrink the slowest error mode, which the next correction would
-  // otherwise have to remove.  Measured on 2048 x 4096, 8 strips, 2000 steps, to e_mis
-  // < 1e-8: 178 + 120 FP32 iterations (this value) against 243 + 61 (1e-7).
-  double inner_rtol = 1e-5;
+  // Tightest relative change an inner solve is asked for.  Its last iterations below
+  // the FP32 residual floor of one correction (about 1e-5 |d|) still shrink the
+  // slowest error mode, which the next correction would otherwise have to remove.
+  double inner_rtol = 1e-7;
   // kept for kfp_swr_set_robin: the constant-in-time forcing (FMODE 1) and its factor
   std::vector<double> Fh_keep;
   double a0_keep = 0.0;
@@ -1218,8 +1216,7 @@ struct kfp_swr {
       const double dnorm = host_scal[1];
       if (!(dnorm > 0)) { converged = tol > 0; break; }
       // Solve the correction only as far as the target needs: the remaining error
-      // must drop by about tol / metric (with margin), and not far below what one FP32
-      // correction can deliver (inner_rtol).
+      // must drop by about tol / metric (with margin), at most to inner_rtol.
       double eta = inner_rtol;
       if (tol > 0) eta = std::min(0.5, std::max(inner_rtol, 0.2 * tol / metric));
       // inner FP32 iterations: delta_0 = d, delta <- M delta + d
