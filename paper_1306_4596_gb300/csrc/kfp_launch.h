@@ -1,12 +1,11 @@
 // kfp_launch.h -- host entry points of the TMA-fed sweep kernels, per precision and
 // tile shape.
 //
-// The kernels of kfp_sweep_tma.cuh, kfp_slot.cuh and kfp_fe_tma.cuh are instantiated, one
-// (precision, shape) pair per
-// translation unit (kfp_launch_<precision>_s<shape>.cu), so that they compile in
-// parallel; host code calls them only through LaunchSet<T, SHAPE> and the runtime
-// choice of shape in kfp_swr.cu (Tma<T>).  Shapes (rows per ring stage CH, ring stages
-// NST, blocks per SM):
+// The kernels of kfp_sweep_tma.cuh, kfp_slot.cuh and kfp_fe_tma.cuh are instantiated,
+// one (precision, shape) pair per translation unit (kfp_launch_<precision>_s<shape>.cu),
+// so that they compile in parallel; host code calls them only through
+// LaunchSet<T, SHAPE> and the runtime choice of shape in kfp_swr.cu (Tma<T>).  Shapes
+// (rows per ring stage CH, ring stages NST, blocks per SM):
 //   0: CH 16, NST 4 (FP64) / 8 (FP32), 1 block per SM  -- about one unit per SM
 //   1: CH  8, NST 4 (FP64) / 8 (FP32), 2 blocks per SM -- several units per SM
 //   2: CH  8, NST 6 (FP64) / 12 (FP32), 2 blocks per SM -- the same, deeper ring
