@@ -86,6 +86,8 @@ def test_null_arguments_are_rejected():
     assert lib.kfp_swr_sweep(None, 1, 0.0, 0, None) == swr.KFP_EINVAL
     assert lib.kfp_swr_traces(None, 0, 0, None, 0) == swr.KFP_EINVAL
     assert lib.kfp_swr_error(None, None, None, None, None, 0) == swr.KFP_EINVAL
+    assert lib.kfp_swr_pipeline_stats(None, None, None, None, None, None) == swr.KFP_EINVAL
+    assert lib.kfp_swr_stats(None, None, None, None, None, None, None) == swr.KFP_EINVAL
     lib.kfp_swr_destroy(None)
     assert lib.kfp_swr_last_error(None) == b""
 

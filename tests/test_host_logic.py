@@ -101,3 +101,16 @@ def test_profiled_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
 def test_job_rate_and_single_rank_time():
     assert bench.job_rate(2, 1_000, 3, 500.0) == pytest.approx(2 * 1_000 * 3 / 0.5)
     assert bench.max_over_ranks(None, None, 1, 12.5) == 12.5
+
+
+def test_depth_flag_bits_do_not_overlap_other_flags():
+    """KFP_FLAG_DEPTH(n) for n = 1..8 and KFP_FLAG_SHAPE(n) for n = 0..2 sit in bits of
+    their own, clear of the single-bit flags."""
+    single = (swr.KFP_FLAG_NO_GRAPH | swr.KFP_FLAG_PROFILE | swr.KFP_FLAG_GENERIC | swr.KFP_FLAG_GAUSS_SEIDEL
+              | swr.KFP_FLAG_NEUMANN_V | swr.KFP_FLAG_PERIODIC_X | swr.KFP_FLAG_SPLIT_SCHEME
+              | swr.KFP_FLAG_PERSISTENT | swr.KFP_FLAG_PER_PASS)
+    for n in range(1, swr.MAX_DEPTH + 1):
+        d = swr.KFP_FLAG_DEPTH(n)
+        assert d & single == 0 and (d >> swr.KFP_FLAG_DEPTH_SHIFT) == n
+        for m in range(swr.TILE_SHAPES):
+            assert d & swr.KFP_FLAG_SHAPE(m) == 0 and swr.KFP_FLAG_SHAPE(m) & single == 0
