@@ -86,7 +86,9 @@ typedef enum { KFP_F64 = 0, KFP_F32 = 1, KFP_MIXED = 2 } kfp_precision;
  * without periodic x; results are bitwise the same either way).  By default the
  * library runs them in one co-resident (cooperative) launch -- the streamed sweep --
  * when a pass has more units (strip x block of 120 columns) than the GPU holds
- * blocks at once, and one launch per pass otherwise (measured faster there). */
+ * blocks at once, and one launch per pass otherwise (measured faster there) -- for a
+ * lone iterate; sweeps of several iterations on smaller grids pipeline iterates
+ * (KFP_FLAG_DEPTH below).  Either flag also turns pipelining off. */
 #define KFP_FLAG_PERSISTENT 128u /* always the streamed sweep */
 #define KFP_FLAG_PER_PASS 256u   /* always one launch per pass */
 /* Tile shape of the TMA-fed sweep (rows per ring stage, ring stages, blocks per SM);
@@ -170,8 +172,11 @@ kfp_status kfp_swr_create(const kfp_swr_desc* desc, const kfp_swr_problem* prob,
  * (0: e_chg, 1: e_mis) is below tol.  tol <= 0 runs exactly max_iters iterations
  * without reading anything back in between.  Iterations continue from the current
  * interface data (calls can be chained).  *iters_done (may be NULL) receives the
- * number of iterations run by this call.
- * Errors: KFP_EINVAL, KFP_ECUDA, KFP_ENOTCONV (tol > 0 not reached), KFP_ENUMERIC.
+ * number of iterations run by this call.  With pipelined iterates (KFP_FLAG_DEPTH)
+ * the tolerance is read after each group of D iterations and the handle is left at
+ * the first iterate that met it: the same count and state as one iterate at a time.
+ * Errors: KFP_EINVAL, KFP_ECUDA, KFP_ENOTCONV (tol > 0 not reached), KFP_ENUMERIC,
+ * KFP_ETIMEOUT (a bounded wait of the streamed sweep expired).
  */
 kfp_status kfp_swr_sweep(kfp_swr_t h, int max_iters, double tol, int tol_kind, int* iters_done);
 
