@@ -114,3 +114,14 @@ def test_depth_flag_bits_do_not_overlap_other_flags():
         assert d & single == 0 and (d >> swr.KFP_FLAG_DEPTH_SHIFT) == n
         for m in range(swr.TILE_SHAPES):
             assert d & swr.KFP_FLAG_SHAPE(m) == 0 and swr.KFP_FLAG_SHAPE(m) & single == 0
+
+
+def test_committed_mixed_workload_record_is_readable_and_consistent():
+    """The bench repeats the committed --mixed-workload record: it parses, both arms
+    reached the tolerance, and the speed-up is the ratio of the two times."""
+    d = bench.committed_mixed_workload()
+    assert d is not None and d["tol"] == 1e-8
+    assert d["f64"]["reached"] and d["mixed"]["reached"]
+    assert d["f64"]["e_mis"] < d["tol"] and d["mixed"]["e_mis"] < d["tol"]
+    assert d["speedup_mixed_vs_f64"] == pytest.approx(d["f64"]["seconds"] / d["mixed"]["seconds"])
+    assert "profiles/mixed_precision_workload.md" in d["source"]
