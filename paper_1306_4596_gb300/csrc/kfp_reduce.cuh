@@ -86,67 +86,72 @@ __global__ void correct_kernel(double* __restrict__ lam_in, const double* __rest
 
 // Error: e_mis = max |lower - upper| over the overlaps, j_l2 = dt hx sum (lower-upper)^2.
 // Also appends (e_mis, e_chg, j_l2) to the device history, e_chg read from *chg and
-// copied to scal[1].  Element e = j per_side + r
-// of the flat range pairs bands[j][0][r] with bands[j][1][r]; the thread's position
-// is advanced by the grid stride instead of being divided out per element, and four
-// elements per thread and round are in flight at once.
+// copied to scal[1].  Interface by interface, bands[j][0][r] is paired with
+// bands[j][1][r] over the grid stride; when per_side is even both sides start on a
+// 16-byte boundary and the values are read in pairs, four pairs per thread and round
+// in flight at once.
 __global__ void __launch_bounds__(kReduceThreads)
 error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double dthx,
              double* partial, unsigned* ticket, const double* chg, double* scal, double* hist, int* iter,
              int hist_cap, int wrap_nxp) {
   // wrap_nxp = nx + 1 with periodic x (column nx repeats column 0 and is left out of
-  // the L2 sum), 0 otherwise
+  // the L2 sum), 0 otherwise; per_side is a multiple of nx + 1, so the column of
+  // value r of a side is r mod (nx + 1)
   double mx = 0.0, sm = 0.0;
-  const size_t n = (size_t)nif * per_side, stride = (size_t)gridDim.x * blockDim.x;
-  const size_t e0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // per_side is a multiple of the row length, so the column of e is e mod (nx + 1)
-  const size_t sj = stride / per_side, sr = stride - sj * per_side;
-  const int scol = wrap_nxp ? (int)(stride % (size_t)wrap_nxp) : 0;
-  struct Pos {
-    size_t lo;  // index of bands[j][0][r]; bands[j][1][r] is lo + per_side
-    size_t r;
-    int m;
-  };
-  auto advance = [&](Pos p) {
-    const size_t r2 = p.r + sr;
-    const size_t wrap = r2 >= per_side ? 1 : 0;
-    p.lo += (2 * (sj + wrap)) * per_side + sr - wrap * per_side;
-    p.r = r2 - wrap * per_side;
-    if (wrap_nxp) {
-      p.m += scol;
-      if (p.m >= wrap_nxp) p.m -= wrap_nxp;
-    }
-    return p;
-  };
-  Pos p;
-  {
-    const size_t j = e0 / per_side;
-    p.r = e0 - j * per_side;
-    p.lo = 2 * j * per_side + p.r;
-    p.m = wrap_nxp ? (int)(e0 % (size_t)wrap_nxp) : 0;
-  }
-  size_t e = e0;
-  for (; e + 3 * stride < n; e += 4 * stride) {
-    Pos q[4];
-    q[0] = p;
-#pragma unroll
-    for (int k = 1; k < 4; ++k) q[k] = advance(q[k - 1]);
-    double lo[4], up[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { lo[k] = bands[q[k].lo]; up[k] = bands[q[k].lo + per_side]; }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double d = lo[k] - up[k];
-      mx = nan_max(mx, fabs(d));
-      if (wrap_nxp == 0 || q[k].m != wrap_nxp - 1) sm += d * d;
-    }
-    p = advance(q[3]);
-  }
-  for (; e < n; e += stride) {
-    const double d = bands[p.lo] - bands[p.lo + per_side];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nxp = (size_t)wrap_nxp;
+  // one value pair d of column m: max and (unless m is the repeated column) sum
+  auto take = [&](double d, size_t m) {
     mx = nan_max(mx, fabs(d));
-    if (wrap_nxp == 0 || p.m != wrap_nxp - 1) sm += d * d;
-    p = advance(p);
+    if (nxp == 0 || m != nxp - 1) sm += d * d;
+  };
+  if ((per_side & 1) == 0) {
+    const size_t n2 = per_side / 2;
+    const size_t m_step = nxp ? (2 * stride) % nxp : 0;
+    for (int j = 0; j < nif; ++j) {
+      const double2* __restrict__ lo = reinterpret_cast<const double2*>(bands + (size_t)2 * j * per_side);
+      const double2* __restrict__ up = reinterpret_cast<const double2*>(bands + ((size_t)2 * j + 1) * per_side);
+      size_t m = nxp ? (2 * t0) % nxp : 0;  // column of the first value of pair e
+      auto next = [&]() {
+        if (nxp) {
+          m += m_step;
+          if (m >= nxp) m -= nxp;
+        }
+      };
+      size_t e = t0;
+      for (; e + 3 * stride < n2; e += 4 * stride) {
+        double2 a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { a[k] = lo[e + k * stride]; b[k] = up[e + k * stride]; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          take(a[k].x - b[k].x, m);
+          take(a[k].y - b[k].y, nxp && m + 1 == nxp ? 0 : m + 1);
+          next();
+        }
+      }
+      for (; e < n2; e += stride) {
+        const double2 a = lo[e], b = up[e];
+        take(a.x - b.x, m);
+        take(a.y - b.y, nxp && m + 1 == nxp ? 0 : m + 1);
+        next();
+      }
+    }
+  } else {
+    const size_t m_step = nxp ? stride % nxp : 0;
+    for (int j = 0; j < nif; ++j) {
+      const double* __restrict__ lo = bands + (size_t)2 * j * per_side;
+      const double* __restrict__ up = lo + per_side;
+      size_t m = nxp ? t0 % nxp : 0;
+      for (size_t e = t0; e < per_side; e += stride) {
+        take(lo[e] - up[e], m);
+        if (nxp) {
+          m += m_step;
+          if (m >= nxp) m -= nxp;
+        }
+      }
+    }
   }
   block_reduce(mx, sm);
   double emis = 0.0, ssum = 0.0;
