@@ -9,6 +9,15 @@
 
 namespace kfp {
 
+// |d| as an integer whose order is that of |d|: the bit pattern without the sign
+// (non-negative doubles order as their bits, and every NaN pattern lies above
+// infinity, so a maximum over these keeps a NaN).  The maxima below run on the
+// integer units; GB300's FP64 pipe is left the subtractions and squares.
+__device__ __forceinline__ unsigned long long abs_key(double d) {
+  return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ double key_value(unsigned long long k) { return __longlong_as_double((long long)k); }
+
 // Exchange: e_chg = max |lam_next - lam_prev| (trace change) into *chg, and
 // lam_dst <- lam_next unless lam_dst is NULL.  lam_dst may be lam_prev (each element
 // is read before it is written, by the same thread).  n is even (the data come in
@@ -17,7 +26,7 @@ namespace kfp {
 __global__ void __launch_bounds__(kReduceThreads)
 exchange_kernel(const double* __restrict__ lam_next, const double* lam_prev, double* lam_dst, size_t n,
                 double* partial, unsigned* ticket, double* chg) {
-  double mx = 0.0, sm = 0.0;
+  unsigned long long mk = 0;
   const double2* __restrict__ nx2 = reinterpret_cast<const double2*>(lam_next);
   const double2* pv2 = reinterpret_cast<const double2*>(lam_prev);
   double2* ds2 = reinterpret_cast<double2*>(lam_dst);
@@ -29,15 +38,16 @@ exchange_kernel(const double* __restrict__ lam_next, const double* lam_prev, dou
     for (int r = 0; r < 4; ++r) { a[r] = nx2[e + r * stride]; b[r] = pv2[e + r * stride]; }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      mx = nan_max(mx, nan_max(fabs(a[r].x - b[r].x), fabs(a[r].y - b[r].y)));
+      mk = max(mk, max(abs_key(a[r].x - b[r].x), abs_key(a[r].y - b[r].y)));
       if (ds2) ds2[e + r * stride] = a[r];
     }
   }
   for (; e < n2; e += stride) {
     const double2 a = nx2[e], b = pv2[e];
-    mx = nan_max(mx, nan_max(fabs(a.x - b.x), fabs(a.y - b.y)));
+    mk = max(mk, max(abs_key(a.x - b.x), abs_key(a.y - b.y)));
     if (ds2) ds2[e] = a;
   }
+  double mx = key_value(mk), sm = 0.0;
   block_reduce(mx, sm);
   last_block_combine(partial, ticket, mx, sm, chg, nullptr);
 }
@@ -97,13 +107,14 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
   // wrap_nxp = nx + 1 with periodic x (column nx repeats column 0 and is left out of
   // the L2 sum), 0 otherwise; per_side is a multiple of nx + 1, so the column of
   // value r of a side is r mod (nx + 1)
-  double mx = 0.0, sm = 0.0;
+  unsigned long long mk = 0;
+  double sm = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nxp = (size_t)wrap_nxp;
   // one value pair d of column m: max and (unless m is the repeated column) sum
   auto take = [&](double d, size_t m) {
-    mx = nan_max(mx, fabs(d));
+    mk = max(mk, abs_key(d));
     if (nxp == 0 || m != nxp - 1) sm += d * d;
   };
   if ((per_side & 1) == 0) {
@@ -153,6 +164,7 @@ error_kernel(const double* __restrict__ bands, int nif, size_t per_side, double 
       }
     }
   }
+  double mx = key_value(mk);
   block_reduce(mx, sm);
   double emis = 0.0, ssum = 0.0;
   if (last_block_combine(partial, ticket, mx, sm, &emis, &ssum) && threadIdx.x == 0) {
